@@ -1,0 +1,215 @@
+/*
+ * pct.h -- C ABI of libpct, a GB300 (sm_103a) implementation of the data-
+ * parallel hot path of the proton-CT data simulator of Witt, Schultze,
+ * Schulte, Schubert and Gomez, "A Proton Simulator for Testing
+ * Implementations of Proton CT Reconstruction Algorithms on GPGPU Clusters".
+ *
+ * The simulator produces the linear system A x = b of Sec. II (Methods):
+ *   x  -- the RSP of every voxel of an analytic NEO phantom (Sec. II-A),
+ *   A  -- one row per proton, a_ij = chord length of proton i's path in
+ *         voxel j (Sec. II-C), stored as CSR (Sec. II-C, Fig. 3),
+ *   b  -- WEPL of proton i, <a_i, x>, optionally with noise (Sec. II-C),
+ * for protons entering as parallel beams from many angles, on straight or
+ * cubic-spline paths with multiple-Coulomb-scattering exit draws (Sec. II-B).
+ *
+ * Conventions of every call:
+ *   - Pointers named *_dev are CUDA device pointers; all others are host.
+ *   - The caller owns every buffer.  The library allocates device memory only
+ *     inside pct_simulate(), and only through the caller's pct_alloc_fn.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
+ *     enqueue their GPU work on it and return without waiting, except where
+ *     a call says it synchronises.
+ *   - Every call returns a pct_status; on failure pct_last_error() returns a
+ *     message for the calling thread.  The library never aborts the process.
+ *   - Row i of A is proton p of angle k with i = k * paths_per_angle + p;
+ *     column j = ix + nx * (iy + ny * iz); voxel ix covers
+ *     [o_x + ix h_x, o_x + (ix+1) h_x) with o_x = -nx h_x / 2 (grid centred
+ *     at the origin).  Beam frame of angle theta: u = (cos, sin, 0) beam
+ *     direction, t = (-sin, cos, 0) lateral, v = (0, 0, 1) (Sec. II-C,
+ *     Givens rotation of the tvu frame into xyz).
+ *   - Results are a pure function of the arguments: the same arguments give
+ *     the same bits.
+ */
+#ifndef PCT_H
+#define PCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PCT_OK = 0,
+  PCT_EINVAL = 1,       /* bad argument: nothing was enqueued */
+  PCT_ENOMEM = 2,       /* the caller's allocator returned NULL / workspace too small */
+  PCT_ECUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
+  PCT_ETIMEOUT = 4,     /* a device-side bounded wait ran out */
+  PCT_EUNSUPPORTED = 5  /* valid request this build does not implement */
+} pct_status;
+
+enum { PCT_ELLIPSOID = 0, PCT_EXTRUDED = 1 };                /* phantom kind (3D) */
+enum { PCT_RASTER_CENTER = 0, PCT_RASTER_CORNER = 1 };       /* Sec. II-A options */
+enum { PCT_PATH_STRAIGHT = 0, PCT_PATH_STRAIGHT_MCS = 1, PCT_PATH_SPLINE = 2 };
+enum { PCT_CHORD_EXACT = 0, PCT_CHORD_CONSTANT = 1 };        /* Sec. II-C */
+enum { PCT_NOISE_NONE = 0, PCT_NOISE_GAUSS_REL = 1 };
+/* Arithmetic form of the path and traversal kernels.  Both give identical
+ * voxel indices and row pointers (every crossing decision equals the FP64
+ * definition's); values and b agree within 1e-6 relative per row.
+ *   PCT_PREC_MIXED: FP32 arithmetic with certified error bounds, exact FP64
+ *                   evaluation only where a bound cannot decide; FP32 lengths,
+ *                   FP32 Kahan-compensated WEPL.
+ *   PCT_PREC_F64:   everything in FP64 (the comparison form).              */
+enum { PCT_PREC_MIXED = 0, PCT_PREC_F64 = 1 };
+
+#define PCT_MAX_REGIONS 16
+#define PCT_MAX_SPLINE_SEGMENTS 1024
+
+/* An ellipse (2D: z ignored) or ellipsoid with centre c and semi-axes a, mm.
+ * Sec. II-A: the NEO phantom is a list of such regions, each with its RSP. */
+typedef struct {
+  double c[3];
+  double a[3];
+  double rsp;
+} pct_region;
+
+/* Sec. II-A.  Regions are painted in order (a later region overwrites an
+ * earlier one where they overlap); region 0 is the phantom's outer boundary,
+ * used as the entry/exit surface of the protons (Sec. II-B).  3D kind
+ * PCT_EXTRUDED tests x, y only (the paper's stacked-slice elliptical
+ * cylinder); PCT_ELLIPSOID tests x, y, z.  n[2] and h[2] are ignored in 2D. */
+typedef struct {
+  int32_t dim;    /* 2 or 3 */
+  int32_t kind;   /* PCT_ELLIPSOID / PCT_EXTRUDED */
+  int32_t raster; /* PCT_RASTER_CENTER / PCT_RASTER_CORNER */
+  int32_t n[3];   /* voxels per axis, >= 1, product < 2^31 */
+  double h[3];    /* voxel size, mm, > 0 */
+  int32_t n_regions;          /* 1..PCT_MAX_REGIONS */
+  const pct_region* regions;  /* host array, copied by pct_phantom_create */
+} pct_phantom_desc;
+
+/* Sec. II-B.  Lateral entry offsets are uniform on t_range (and v_range in
+ * 3D).  MCS models draw, per proton, an entry slope ~ N(0, sigma_in) per
+ * plane and a bivariate normal exit pair (displacement ~ N(0, sigma_lat) mm,
+ * slope ~ N(0, sigma_out)) with correlation rho per plane.  SPLINE paths are
+ * cubic Hermite curves sampled at spline_segments pieces.  With
+ * PCT_NOISE_GAUSS_REL, b_i is multiplied by (1 + noise_rel z_i), z_i ~ N(0,1)
+ * (our stand-in for the PSTAR / Tschalar energy-straggling noise of
+ * Sec. II-C, whose tables are not part of this library). */
+typedef struct {
+  int32_t model;           /* PCT_PATH_* */
+  int32_t chord;           /* PCT_CHORD_*: CONSTANT stores h_x in A, b stays exact */
+  int32_t spline_segments; /* 1..PCT_MAX_SPLINE_SEGMENTS (SPLINE only) */
+  int32_t noise;           /* PCT_NOISE_* */
+  double t_range[2];
+  double v_range[2];
+  double sigma_lat, sigma_in, sigma_out, rho; /* |rho| <= 1 */
+  double noise_rel;
+} pct_path_model;
+
+/* One simulated acquisition: angles (host, radians), protons per angle, the
+ * path model, and the generator key (seed, stream_id).  Random numbers come
+ * from Philox4x64-10 (Salmon et al., SC'11) with key (seed, stream_id) and
+ * counter (row, block, 0, 0), replacing the paper's rand(). */
+typedef struct {
+  const double* angles_rad;
+  int32_t n_angles;
+  int64_t paths_per_angle;
+  pct_path_model model;
+  uint64_t seed;
+  uint64_t stream_id;
+} pct_geometry;
+
+typedef struct pct_phantom pct_phantom; /* opaque, host memory only */
+
+/* CSR A plus b and x (Sec. II-C, Fig. 3).  All pointers are device pointers.
+ * row_ptr: int64 [n_rows + 1]; col: int32 [nnz]; val: float [nnz] (chord
+ * lengths, mm); b: float [n_rows] (WEPL, mm); x_true: float [n_cols]. */
+typedef struct {
+  int64_t n_rows, n_cols, nnz;
+  int64_t* row_ptr;
+  int32_t* col;
+  float* val;
+  float* b;
+  float* x_true;
+} pct_csr;
+
+typedef void* (*pct_alloc_fn)(size_t bytes, void* ctx); /* device memory or NULL */
+typedef void (*pct_free_fn)(void* ptr, void* ctx);
+
+/* ---- phantom (Sec. II-A) ---------------------------------------------- */
+
+/* Validates and copies the description.  EINVAL on bad sizes, axes or
+ * counts; ENOMEM if host memory runs out.  *out is released by
+ * pct_phantom_destroy. */
+pct_status pct_phantom_create(const pct_phantom_desc* desc, pct_phantom** out);
+pct_status pct_phantom_destroy(pct_phantom* ph);
+/* number of voxels (columns of A), or -1 for NULL */
+int64_t pct_phantom_nvox(const pct_phantom* ph);
+
+/* Sec. II-A: x_true_dev[j] = RSP of voxel j by the phantom's raster option
+ * (centre point, or the mean over the 4 / 8 corners), in FP32.  The stored
+ * solution vector of the simulator. */
+pct_status pct_phantom_rasterize(const pct_phantom* ph, float* x_true_dev, void* stream);
+
+/* ---- simulation: A, b (Sec. II-B, II-C) -------------------------------- */
+
+/* Bytes of device workspace that pct_simulate_count / _fill / pct_forward /
+ * pct_adjoint need for this geometry (angle table, spline basis, per-row
+ * path records, scan partials). */
+pct_status pct_simulate_workspace_size(const pct_phantom* ph, const pct_geometry* geo,
+                                       int32_t precision, size_t* bytes);
+
+/* Phase 1: row_ptr_dev[0..n_rows] = exclusive scan of the row lengths (int64).
+ * nnz = row_ptr_dev[n_rows] (read it back to size col / val).  Also leaves
+ * the per-row path records in the workspace for phase 2.  Protons whose
+ * path misses the grid get empty rows. */
+pct_status pct_simulate_count(const pct_phantom* ph, const pct_geometry* geo, int32_t precision,
+                              void* workspace_dev, size_t workspace_bytes, int64_t* row_ptr_dev,
+                              void* stream);
+
+/* Phase 2, after pct_simulate_count with the same arguments and workspace:
+ * writes col_dev / val_dev at row_ptr_dev (entries of a row in path order,
+ * voxels re-entered later in a row appear again) and b_dev (WEPL from the
+ * exact chord lengths and x_true_dev, then noise). */
+pct_status pct_simulate_fill(const pct_phantom* ph, const pct_geometry* geo, int32_t precision,
+                             void* workspace_dev, size_t workspace_bytes,
+                             const int64_t* row_ptr_dev, const float* x_true_dev,
+                             int32_t* col_dev, float* val_dev, float* b_dev, void* stream);
+
+/* Whole simulation: rasterises x_true, counts, reads nnz back (synchronises
+ * the stream once), allocates through alloc_fn and fills.  out receives
+ * device buffers owned by the caller (free them with free_fn).  On failure
+ * everything allocated so far is freed. */
+pct_status pct_simulate(const pct_phantom* ph, const pct_geometry* geo, int32_t precision,
+                        pct_alloc_fn alloc_fn, pct_free_fn free_fn, void* ctx, pct_csr* out,
+                        void* stream);
+
+/* ---- projectors: y = A x and g += A^T r (Sec. II, A x = b) -------------- */
+
+/* y_dev[i] = sum_j A_ij x_dev[j] for rows [row0, row0 + n_rows).  With
+ * A != NULL the CSR is used (row indices are global; y_dev has n_rows
+ * entries); with A == NULL the rows are regenerated from the geometry
+ * (matrix-free, paths recomputed) with exact chord lengths. */
+pct_status pct_forward(const pct_phantom* ph, const pct_geometry* geo, const pct_csr* A,
+                       int64_t row0, int64_t n_rows, const float* x_dev, float* y_dev,
+                       void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* g_dev[j] += sum_i A_ij r_dev[i - row0] over rows [row0, row0 + n_rows)
+ * (accumulates, so chunks can be summed; the caller zeroes g_dev first).
+ * FP32 atomic accumulation: the order of additions is not fixed. */
+pct_status pct_adjoint(const pct_phantom* ph, const pct_geometry* geo, const pct_csr* A,
+                       int64_t row0, int64_t n_rows, const float* r_dev, float* g_dev,
+                       void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* message of the calling thread's last failure ("" if none) */
+const char* pct_last_error(void);
+
+/* library version string */
+const char* pct_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCT_H */

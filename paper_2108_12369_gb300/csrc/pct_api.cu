@@ -1,0 +1,392 @@
+// pct_api.cu -- the C ABI of include/pct.h: argument checks, workspace
+// layout, host-side tables (angle cos/sin from the host libm, Hermite basis)
+// and the launch sequences.  Host code here is compiled without FMA
+// contraction so that its tables equal the definition bit for bit.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pct_kernels.cuh"
+
+using namespace pct;
+
+namespace {
+
+thread_local std::string g_err;
+
+pct_status fail(pct_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+pct_status cuda_check(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(PCT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  return PCT_OK;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct pct_phantom {
+  pct_phantom_desc desc;
+  pct_region regions[PCT_MAX_REGIONS];
+  PhantomDev dev;
+  long long nvox;
+};
+
+// ---------------------------------------------------------------------------
+// phantom
+// ---------------------------------------------------------------------------
+extern "C" pct_status pct_phantom_create(const pct_phantom_desc* d, pct_phantom** out) {
+  if (!d || !out) return fail(PCT_EINVAL, "pct_phantom_create: NULL argument");
+  *out = nullptr;
+  if (d->dim != 2 && d->dim != 3) return fail(PCT_EINVAL, "dim must be 2 or 3 (got %d)", d->dim);
+  if (d->kind != PCT_ELLIPSOID && d->kind != PCT_EXTRUDED) return fail(PCT_EINVAL, "bad phantom kind %d", d->kind);
+  if (d->raster != PCT_RASTER_CENTER && d->raster != PCT_RASTER_CORNER)
+    return fail(PCT_EINVAL, "bad raster option %d", d->raster);
+  long long nvox = 1;
+  for (int a = 0; a < d->dim; ++a) {
+    if (d->n[a] < 1) return fail(PCT_EINVAL, "n[%d] = %d must be >= 1", a, d->n[a]);
+    if (!finite_pos(d->h[a])) return fail(PCT_EINVAL, "h[%d] must be finite and > 0", a);
+    nvox *= d->n[a];
+    if (nvox >= (1LL << 31)) return fail(PCT_EINVAL, "grid has >= 2^31 voxels");
+  }
+  if (d->n_regions < 1 || d->n_regions > PCT_MAX_REGIONS)
+    return fail(PCT_EINVAL, "n_regions = %d outside 1..%d", d->n_regions, PCT_MAX_REGIONS);
+  if (!d->regions) return fail(PCT_EINVAL, "regions is NULL");
+  for (int r = 0; r < d->n_regions; ++r) {
+    const pct_region& R = d->regions[r];
+    int axes = (d->dim == 3) ? 3 : 2;
+    for (int a = 0; a < axes; ++a) {
+      if (!finite_pos(R.a[a])) return fail(PCT_EINVAL, "region %d semi-axis %d must be finite and > 0", r, a);
+      if (!std::isfinite(R.c[a])) return fail(PCT_EINVAL, "region %d centre must be finite", r);
+    }
+    if (!std::isfinite(R.rsp)) return fail(PCT_EINVAL, "region %d RSP must be finite", r);
+  }
+  pct_phantom* ph = new (std::nothrow) pct_phantom;
+  if (!ph) return fail(PCT_ENOMEM, "out of host memory");
+  memset(ph, 0, sizeof(*ph));
+  ph->desc = *d;
+  memcpy(ph->regions, d->regions, sizeof(pct_region) * d->n_regions);
+  ph->desc.regions = ph->regions;
+  for (int a = d->dim; a < 3; ++a) {
+    ph->desc.n[a] = 1;
+    ph->desc.h[a] = 1.0;
+  }
+  ph->nvox = nvox;
+  PhantomDev& pd = ph->dev;
+  pd.g.dim = d->dim;
+  for (int a = 0; a < 3; ++a) {
+    pd.g.n[a] = ph->desc.n[a];
+    pd.g.h[a] = ph->desc.h[a];
+    pd.g.o[a] = -0.5 * ((double)pd.g.n[a] * pd.g.h[a]);
+  }
+  pd.kind = d->kind;
+  pd.raster = d->raster;
+  pd.n_regions = d->n_regions;
+  for (int r = 0; r < d->n_regions; ++r) {
+    for (int a = 0; a < 3; ++a) {
+      pd.c[r][a] = ph->regions[r].c[a];
+      double ax = (a < d->dim) ? ph->regions[r].a[a] : 1.0;
+      if (!(ax > 0.0)) ax = 1.0;
+      pd.a[r][a] = ax;
+      pd.ra[r][a] = 1.0 / ax;
+    }
+    pd.rsp[r] = ph->regions[r].rsp;
+  }
+  *out = ph;
+  return PCT_OK;
+}
+
+extern "C" pct_status pct_phantom_destroy(pct_phantom* ph) {
+  delete ph;
+  return PCT_OK;
+}
+
+extern "C" int64_t pct_phantom_nvox(const pct_phantom* ph) { return ph ? ph->nvox : -1; }
+
+extern "C" pct_status pct_phantom_rasterize(const pct_phantom* ph, float* x, void* stream) {
+  if (!ph || !x) return fail(PCT_EINVAL, "pct_phantom_rasterize: NULL argument");
+  launch_raster(ph->dev, x, ph->nvox, (cudaStream_t)stream);
+  return cuda_check("raster launch");
+}
+
+// ---------------------------------------------------------------------------
+// geometry, workspace, tables
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Layout {
+  size_t cs, basis, partial, rec, total;
+  long long rows;
+  int K;
+};
+
+pct_status check_geometry(const pct_phantom* ph, const pct_geometry* g, int precision) {
+  if (!ph || !g) return fail(PCT_EINVAL, "NULL phantom or geometry");
+  if (precision != PCT_PREC_MIXED && precision != PCT_PREC_F64)
+    return fail(PCT_EINVAL, "bad precision %d", precision);
+  if (g->n_angles < 0 || g->paths_per_angle < 0) return fail(PCT_EINVAL, "negative angle or path count");
+  if (g->n_angles > 0 && !g->angles_rad) return fail(PCT_EINVAL, "angles_rad is NULL");
+  for (int k = 0; k < g->n_angles; ++k)
+    if (!std::isfinite(g->angles_rad[k])) return fail(PCT_EINVAL, "angle %d is not finite", k);
+  long long rows = (long long)g->n_angles * g->paths_per_angle;
+  if (g->paths_per_angle > 0 && rows / g->paths_per_angle != g->n_angles) return fail(PCT_EINVAL, "row count overflows");
+  if (rows > (1LL << 40)) return fail(PCT_EINVAL, "more than 2^40 rows");
+  const pct_path_model& m = g->model;
+  if (m.model < PCT_PATH_STRAIGHT || m.model > PCT_PATH_SPLINE) return fail(PCT_EINVAL, "bad path model %d", m.model);
+  if (m.chord != PCT_CHORD_EXACT && m.chord != PCT_CHORD_CONSTANT) return fail(PCT_EINVAL, "bad chord option %d", m.chord);
+  if (m.noise != PCT_NOISE_NONE && m.noise != PCT_NOISE_GAUSS_REL) return fail(PCT_EINVAL, "bad noise option %d", m.noise);
+  if (m.model == PCT_PATH_SPLINE && (m.spline_segments < 1 || m.spline_segments > PCT_MAX_SPLINE_SEGMENTS))
+    return fail(PCT_EINVAL, "spline_segments = %d outside 1..%d", m.spline_segments, PCT_MAX_SPLINE_SEGMENTS);
+  for (int q = 0; q < 2; ++q)
+    if (!std::isfinite(m.t_range[q]) || !std::isfinite(m.v_range[q])) return fail(PCT_EINVAL, "entry ranges must be finite");
+  if (m.t_range[0] > m.t_range[1] || m.v_range[0] > m.v_range[1]) return fail(PCT_EINVAL, "entry range lo > hi");
+  const double sig[4] = {m.sigma_lat, m.sigma_in, m.sigma_out, m.noise_rel};
+  for (double s : sig)
+    if (!std::isfinite(s) || s < 0.0) return fail(PCT_EINVAL, "sigmas must be finite and >= 0");
+  if (!std::isfinite(m.rho) || m.rho < -1.0 || m.rho > 1.0) return fail(PCT_EINVAL, "rho must lie in [-1, 1]");
+  return PCT_OK;
+}
+
+Layout layout_of(const pct_phantom*, const pct_geometry* g, int precision) {
+  Layout L;
+  L.rows = (long long)g->n_angles * g->paths_per_angle;
+  L.K = (g->model.model == PCT_PATH_SPLINE) ? g->model.spline_segments : 1;
+  size_t off = 0;
+  L.cs = off;
+  off = align256(off + sizeof(double2) * (size_t)(g->n_angles > 0 ? g->n_angles : 1));
+  L.basis = off;
+  off = align256(off + sizeof(Basis4) * (size_t)(L.K + 1));
+  L.partial = off;
+  off = align256(off + sizeof(long long) * (size_t)scan_partials_needed(L.rows));
+  L.rec = off;
+  L.total = off;
+  return L;
+}
+
+// the simulation's kernel arguments; uploads the angle and basis tables
+pct_status make_sim(const pct_phantom* ph, const pct_geometry* g, int precision, void* ws, size_t ws_bytes,
+                    cudaStream_t st, SimDev& S, Layout& L) {
+  pct_status rc = check_geometry(ph, g, precision);
+  if (rc != PCT_OK) return rc;
+  L = layout_of(ph, g, precision);
+  if (!ws || ws_bytes < L.total)
+    return fail(PCT_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed", ws_bytes, L.total);
+  memset(&S, 0, sizeof(S));
+  S.ph = ph->dev;
+  const pct_path_model& m = g->model;
+  S.md.model = m.model;
+  S.md.chord = m.chord;
+  S.md.K = L.K;
+  S.md.noise = m.noise;
+  S.md.t_lo = m.t_range[0];
+  S.md.t_hi = m.t_range[1];
+  S.md.v_lo = m.v_range[0];
+  S.md.v_hi = m.v_range[1];
+  S.md.sigma_lat = m.sigma_lat;
+  S.md.sigma_in = m.sigma_in;
+  S.md.sigma_out = m.sigma_out;
+  S.md.rho = m.rho;
+  S.md.rho_c = std::sqrt(1.0 - m.rho * m.rho);
+  S.md.noise_rel = m.noise_rel;
+  S.n_angles = g->n_angles;
+  S.P = g->paths_per_angle;
+  S.seed = g->seed;
+  S.stream = g->stream_id;
+  double diag2 = 0.0;
+  for (int a = 0; a < ph->dev.g.dim; ++a) {
+    double w = (double)ph->dev.g.n[a] * ph->dev.g.h[a];
+    diag2 = diag2 + w * w;
+  }
+  S.R = 2.0 * std::sqrt(diag2);
+  char* base = (char*)ws;
+  S.cs = (const double2*)(base + L.cs);
+  S.basis = (const Basis4*)(base + L.basis);
+
+  std::vector<double2> cs((size_t)(g->n_angles > 0 ? g->n_angles : 1));
+  for (int k = 0; k < g->n_angles; ++k) {
+    cs[k].x = std::cos(g->angles_rad[k]);
+    cs[k].y = std::sin(g->angles_rad[k]);
+  }
+  std::vector<Basis4> bs((size_t)L.K + 1);
+  for (int j = 0; j <= L.K; ++j) {
+    double sp = (double)j / (double)L.K;
+    double s2 = sp * sp;
+    double s3 = s2 * sp;
+    bs[j].h00 = (2.0 * s3 - 3.0 * s2) + 1.0;
+    bs[j].h10 = (s3 - 2.0 * s2) + sp;
+    bs[j].h01 = 3.0 * s2 - 2.0 * s3;
+    bs[j].h11 = s3 - s2;
+  }
+  // the host vectors are pageable: the copies return once they are staged
+  if (cudaMemcpyAsync(base + L.cs, cs.data(), sizeof(double2) * cs.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(base + L.basis, bs.data(), sizeof(Basis4) * bs.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return cuda_check("table upload");
+  return PCT_OK;
+}
+
+}  // namespace
+
+extern "C" pct_status pct_simulate_workspace_size(const pct_phantom* ph, const pct_geometry* g, int32_t precision,
+                                                  size_t* bytes) {
+  if (!bytes) return fail(PCT_EINVAL, "bytes is NULL");
+  pct_status rc = check_geometry(ph, g, precision);
+  if (rc != PCT_OK) return rc;
+  *bytes = layout_of(ph, g, precision).total;
+  return PCT_OK;
+}
+
+extern "C" pct_status pct_simulate_count(const pct_phantom* ph, const pct_geometry* g, int32_t precision, void* ws,
+                                         size_t ws_bytes, int64_t* row_ptr, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  SimDev S;
+  Layout L;
+  pct_status rc = make_sim(ph, g, precision, ws, ws_bytes, st, S, L);
+  if (rc != PCT_OK) return rc;
+  if (!row_ptr) return fail(PCT_EINVAL, "row_ptr is NULL");
+  long long* rp = (long long*)row_ptr;
+  if (precision != PCT_PREC_F64) return fail(PCT_EUNSUPPORTED, "the mixed form is not built yet");
+  launch_count_f64(S, 0, L.rows, rp + 1, st);
+  if ((rc = cuda_check("count launch")) != PCT_OK) return rc;
+  launch_scan_rowptr(rp, L.rows, (long long*)((char*)ws + L.partial), st);
+  return cuda_check("scan launch");
+}
+
+extern "C" pct_status pct_simulate_fill(const pct_phantom* ph, const pct_geometry* g, int32_t precision, void* ws,
+                                        size_t ws_bytes, const int64_t* row_ptr, const float* x, int32_t* col,
+                                        float* val, float* b, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  SimDev S;
+  Layout L;
+  pct_status rc = make_sim(ph, g, precision, ws, ws_bytes, st, S, L);
+  if (rc != PCT_OK) return rc;
+  if (L.rows > 0 && (!row_ptr || !x || !b)) return fail(PCT_EINVAL, "NULL row_ptr, x_true or b");
+  const long long* rp = (const long long*)row_ptr;
+  if (precision != PCT_PREC_F64) return fail(PCT_EUNSUPPORTED, "the mixed form is not built yet");
+  launch_fill_f64(S, 0, L.rows, rp, x, (int*)col, val, b, st);
+  return cuda_check("fill launch");
+}
+
+extern "C" pct_status pct_simulate(const pct_phantom* ph, const pct_geometry* g, int32_t precision,
+                                   pct_alloc_fn alloc_fn, pct_free_fn free_fn, void* ctx, pct_csr* out,
+                                   void* stream) {
+  if (!alloc_fn || !free_fn || !out) return fail(PCT_EINVAL, "pct_simulate: NULL allocator or output");
+  cudaStream_t st = (cudaStream_t)stream;
+  pct_status rc = check_geometry(ph, g, precision);
+  if (rc != PCT_OK) return rc;
+  memset(out, 0, sizeof(*out));
+  Layout L = layout_of(ph, g, precision);
+  void* ws = nullptr;
+  pct_csr c;
+  memset(&c, 0, sizeof(c));
+  c.n_rows = L.rows;
+  c.n_cols = ph->nvox;
+  auto cleanup = [&]() {
+    if (ws) free_fn(ws, ctx);
+    if (c.row_ptr) free_fn(c.row_ptr, ctx);
+    if (c.col) free_fn(c.col, ctx);
+    if (c.val) free_fn(c.val, ctx);
+    if (c.b) free_fn(c.b, ctx);
+    if (c.x_true) free_fn(c.x_true, ctx);
+  };
+  ws = alloc_fn(L.total, ctx);
+  c.x_true = (float*)alloc_fn(sizeof(float) * (size_t)ph->nvox, ctx);
+  c.row_ptr = (int64_t*)alloc_fn(sizeof(int64_t) * (size_t)(L.rows + 1), ctx);
+  c.b = (float*)alloc_fn(sizeof(float) * (size_t)(L.rows > 0 ? L.rows : 1), ctx);
+  if (!ws || !c.x_true || !c.row_ptr || !c.b) {
+    cleanup();
+    return fail(PCT_ENOMEM, "allocator returned NULL");
+  }
+  if ((rc = pct_phantom_rasterize(ph, c.x_true, stream)) != PCT_OK ||
+      (rc = pct_simulate_count(ph, g, precision, ws, L.total, c.row_ptr, stream)) != PCT_OK) {
+    cleanup();
+    return rc;
+  }
+  long long nnz = 0;
+  if (cudaMemcpyAsync(&nnz, c.row_ptr + L.rows, sizeof(long long), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cleanup();
+    return cuda_check("reading nnz");
+  }
+  c.nnz = nnz;
+  c.col = (int32_t*)alloc_fn(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1), ctx);
+  c.val = (float*)alloc_fn(sizeof(float) * (size_t)(nnz > 0 ? nnz : 1), ctx);
+  if (!c.col || !c.val) {
+    cleanup();
+    return fail(PCT_ENOMEM, "allocator returned NULL for %lld nonzeros", nnz);
+  }
+  if ((rc = pct_simulate_fill(ph, g, precision, ws, L.total, c.row_ptr, c.x_true, c.col, c.val, c.b, stream)) !=
+      PCT_OK) {
+    cleanup();
+    return rc;
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    cleanup();
+    return cuda_check("fill");
+  }
+  free_fn(ws, ctx);
+  *out = c;
+  return PCT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// projectors
+// ---------------------------------------------------------------------------
+extern "C" pct_status pct_forward(const pct_phantom* ph, const pct_geometry* g, const pct_csr* A, int64_t row0,
+                                  int64_t n_rows, const float* x, float* y, void* ws, size_t ws_bytes, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!x || !y) return fail(PCT_EINVAL, "pct_forward: NULL x or y");
+  if (row0 < 0 || n_rows < 0) return fail(PCT_EINVAL, "negative row range");
+  if (A) {
+    if (!A->row_ptr || !A->col || !A->val) return fail(PCT_EINVAL, "incomplete CSR");
+    if (row0 + n_rows > A->n_rows) return fail(PCT_EINVAL, "row range beyond the CSR");
+    launch_csr_forward((const long long*)A->row_ptr, A->col, A->val, row0, n_rows, x, y, st);
+    return cuda_check("csr forward");
+  }
+  SimDev S;
+  Layout L;
+  pct_status rc = make_sim(ph, g, PCT_PREC_F64, ws, ws_bytes, st, S, L);
+  if (rc != PCT_OK) return rc;
+  if (row0 + n_rows > L.rows) return fail(PCT_EINVAL, "row range beyond the geometry");
+  launch_mf_forward_f64(S, row0, n_rows, x, y, st);
+  return cuda_check("matrix-free forward");
+}
+
+extern "C" pct_status pct_adjoint(const pct_phantom* ph, const pct_geometry* g, const pct_csr* A, int64_t row0,
+                                  int64_t n_rows, const float* r, float* gout, void* ws, size_t ws_bytes,
+                                  void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!r || !gout) return fail(PCT_EINVAL, "pct_adjoint: NULL r or g");
+  if (row0 < 0 || n_rows < 0) return fail(PCT_EINVAL, "negative row range");
+  if (A) {
+    if (!A->row_ptr || !A->col || !A->val) return fail(PCT_EINVAL, "incomplete CSR");
+    if (row0 + n_rows > A->n_rows) return fail(PCT_EINVAL, "row range beyond the CSR");
+    launch_csr_adjoint((const long long*)A->row_ptr, A->col, A->val, row0, n_rows, r, gout, st);
+    return cuda_check("csr adjoint");
+  }
+  SimDev S;
+  Layout L;
+  pct_status rc = make_sim(ph, g, PCT_PREC_F64, ws, ws_bytes, st, S, L);
+  if (rc != PCT_OK) return rc;
+  if (row0 + n_rows > L.rows) return fail(PCT_EINVAL, "row range beyond the geometry");
+  launch_mf_adjoint_f64(S, row0, n_rows, r, gout, st);
+  return cuda_check("matrix-free adjoint");
+}
+
+extern "C" const char* pct_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char* pct_version(void) { return "libpct 0.1 (sm_103a)"; }

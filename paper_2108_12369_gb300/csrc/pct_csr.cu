@@ -1,0 +1,51 @@
+// pct_csr.cu -- projectors on an explicit CSR A (Sec. II, A x = b):
+// y = A x (one warp per row, coalesced col/val reads, FP32 accumulation)
+// and g += A^T r (one warp per row, FP32 atomics on g).  Both are HBM-bound
+// at 8 bytes per nonzero.
+#include "pct_kernels.cuh"
+
+namespace pct {
+
+__global__ void k_csr_forward(const long long* __restrict__ row_ptr, const int* __restrict__ col,
+                              const float* __restrict__ val, long long row0, long long n,
+                              const float* __restrict__ x, float* __restrict__ y) {
+  long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  long long r = row0 + w;
+  long long beg = row_ptr[r], end = row_ptr[r + 1];
+  float acc = 0.0f;
+  for (long long e = beg + lane; e < end; e += 32) acc = fmaf(__ldg(val + e), __ldg(x + __ldg(col + e)), acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) y[w] = acc;
+}
+
+__global__ void k_csr_adjoint(const long long* __restrict__ row_ptr, const int* __restrict__ col,
+                              const float* __restrict__ val, long long row0, long long n,
+                              const float* __restrict__ r, float* __restrict__ g) {
+  long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  float ri = r[w];
+  if (ri == 0.0f) return;
+  long long rr = row0 + w;
+  long long beg = row_ptr[rr], end = row_ptr[rr + 1];
+  for (long long e = beg + lane; e < end; e += 32) atomicAdd(g + __ldg(col + e), __ldg(val + e) * ri);
+}
+
+void launch_csr_forward(const long long* row_ptr, const int* col, const float* val, long long row0,
+                        long long n, const float* x, float* y, cudaStream_t st) {
+  if (n <= 0) return;
+  long long threads = n * 32;
+  k_csr_forward<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(row_ptr, col, val, row0, n, x, y);
+}
+
+void launch_csr_adjoint(const long long* row_ptr, const int* col, const float* val, long long row0,
+                        long long n, const float* r, float* g, cudaStream_t st) {
+  if (n <= 0) return;
+  long long threads = n * 32;
+  k_csr_adjoint<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(row_ptr, col, val, row0, n, r, g);
+}
+
+}  // namespace pct

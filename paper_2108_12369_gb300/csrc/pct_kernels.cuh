@@ -1,0 +1,33 @@
+// pct_kernels.cuh -- launchers of the libpct kernels (host-callable).
+#pragma once
+#include "pct_device.cuh"
+
+namespace pct {
+
+// rows scanned per block by the row-pointer scan
+constexpr int kScanTile = 4096;
+
+void launch_raster(const PhantomDev& ph, float* x, long long nvox, cudaStream_t st);
+
+// all-FP64 form (pct_f64.cu)
+void launch_count_f64(const SimDev& S, long long row0, long long n, long long* counts, cudaStream_t st);
+void launch_fill_f64(const SimDev& S, long long row0, long long n, const long long* row_ptr,
+                     const float* x, int* col, float* val, float* b, cudaStream_t st);
+void launch_mf_forward_f64(const SimDev& S, long long row0, long long n, const float* x, float* y,
+                           cudaStream_t st);
+void launch_mf_adjoint_f64(const SimDev& S, long long row0, long long n, const float* r, float* g,
+                           cudaStream_t st);
+
+// row pointers (pct_scan.cu): row_ptr[0] = 0, row_ptr[1..n] = inclusive scan
+// of the counts already stored in row_ptr[1..n]; partial holds
+// ceil(n / kScanTile) + 1 int64 of scratch.
+long long scan_partials_needed(long long n);
+void launch_scan_rowptr(long long* row_ptr, long long n, long long* partial, cudaStream_t st);
+
+// CSR projectors (pct_csr.cu)
+void launch_csr_forward(const long long* row_ptr, const int* col, const float* val, long long row0,
+                        long long n, const float* x, float* y, cudaStream_t st);
+void launch_csr_adjoint(const long long* row_ptr, const int* col, const float* val, long long row0,
+                        long long n, const float* r, float* g, cudaStream_t st);
+
+}  // namespace pct

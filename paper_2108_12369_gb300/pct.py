@@ -1,0 +1,262 @@
+"""Python binding of libpct (include/pct.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module turns PyTorch
+tensors into device pointers and workload dicts into the C structs.  It
+raises if libpct.so is missing: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+from . import workloads as W
+
+LIB_PATH = Path(__file__).resolve().parent / "_build" / "libpct.so"
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
+PREC_MIXED, PREC_F64 = 0, 1
+MAX_REGIONS = 16
+
+
+class PctError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libpct status {status}: {msg}")
+        self.status = status
+
+
+class Region(C.Structure):
+    _fields_ = [("c", C.c_double * 3), ("a", C.c_double * 3), ("rsp", C.c_double)]
+
+
+class PhantomDesc(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("kind", C.c_int32), ("raster", C.c_int32),
+                ("n", C.c_int32 * 3), ("h", C.c_double * 3), ("n_regions", C.c_int32),
+                ("regions", C.POINTER(Region))]
+
+
+class PathModel(C.Structure):
+    _fields_ = [("model", C.c_int32), ("chord", C.c_int32), ("spline_segments", C.c_int32),
+                ("noise", C.c_int32), ("t_range", C.c_double * 2), ("v_range", C.c_double * 2),
+                ("sigma_lat", C.c_double), ("sigma_in", C.c_double), ("sigma_out", C.c_double),
+                ("rho", C.c_double), ("noise_rel", C.c_double)]
+
+
+class Geometry(C.Structure):
+    _fields_ = [("angles_rad", C.POINTER(C.c_double)), ("n_angles", C.c_int32),
+                ("paths_per_angle", C.c_int64), ("model", PathModel), ("seed", C.c_uint64),
+                ("stream_id", C.c_uint64)]
+
+
+class Csr(C.Structure):
+    _fields_ = [("n_rows", C.c_int64), ("n_cols", C.c_int64), ("nnz", C.c_int64),
+                ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p),
+                ("b", C.c_void_p), ("x_true", C.c_void_p)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+# every symbol include/pct.h declares
+EXPORTS = ["pct_phantom_create", "pct_phantom_destroy", "pct_phantom_nvox", "pct_phantom_rasterize",
+           "pct_simulate_workspace_size", "pct_simulate_count", "pct_simulate_fill", "pct_simulate",
+           "pct_forward", "pct_adjoint", "pct_last_error", "pct_version"]
+
+_lib = None
+
+
+def lib():
+    """Load libpct.so (built by build.build()); raises when it is missing."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2108_12369_gb300.build.build()")
+        L = C.CDLL(str(LIB_PATH))
+        P, vp = C.POINTER, C.c_void_p
+        sig = {
+            "pct_phantom_create": ([P(PhantomDesc), P(vp)], C.c_int),
+            "pct_phantom_destroy": ([vp], C.c_int),
+            "pct_phantom_nvox": ([vp], C.c_int64),
+            "pct_phantom_rasterize": ([vp, vp, vp], C.c_int),
+            "pct_simulate_workspace_size": ([vp, P(Geometry), C.c_int32, P(C.c_size_t)], C.c_int),
+            "pct_simulate_count": ([vp, P(Geometry), C.c_int32, vp, C.c_size_t, vp, vp], C.c_int),
+            "pct_simulate_fill": ([vp, P(Geometry), C.c_int32, vp, C.c_size_t, vp, vp, vp, vp, vp, vp],
+                                  C.c_int),
+            "pct_simulate": ([vp, P(Geometry), C.c_int32, ALLOC_FN, FREE_FN, vp, P(Csr), vp], C.c_int),
+            "pct_forward": ([vp, P(Geometry), P(Csr), C.c_int64, C.c_int64, vp, vp, vp, C.c_size_t, vp],
+                            C.c_int),
+            "pct_adjoint": ([vp, P(Geometry), P(Csr), C.c_int64, C.c_int64, vp, vp, vp, C.c_size_t, vp],
+                            C.c_int),
+            "pct_last_error": ([], C.c_char_p),
+            "pct_version": ([], C.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise PctError(status, lib().pct_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def last_error() -> str:
+    return lib().pct_last_error().decode()
+
+
+def version() -> str:
+    return lib().pct_version().decode()
+
+
+class Phantom:
+    """Handle of pct_phantom_create(desc) for a workloads.phantom() dict."""
+
+    def __init__(self, desc: dict):
+        regs = desc["regions"]
+        if not 1 <= len(regs) <= MAX_REGIONS:
+            raise ValueError("1..16 regions")
+        self._regs = (Region * len(regs))(*[Region((C.c_double * 3)(*r["c"]), (C.c_double * 3)(*r["a"]),
+                                                   r["rsp"]) for r in regs])
+        n = list(desc["n"]) + [1] * (3 - len(desc["n"]))
+        h = list(desc["h"]) + [1.0] * (3 - len(desc["h"]))
+        self._desc = PhantomDesc(desc["dim"], desc.get("kind", W.ELLIPSOID), desc.get("raster", W.CORNER),
+                                 (C.c_int32 * 3)(*n), (C.c_double * 3)(*h), len(regs),
+                                 C.cast(self._regs, C.POINTER(Region)))
+        self.handle = C.c_void_p()
+        _check(lib().pct_phantom_create(C.byref(self._desc), C.byref(self.handle)))
+        self.nvox = int(lib().pct_phantom_nvox(self.handle))
+        self.desc = desc
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.pct_phantom_destroy(self.handle)
+            self.handle = None
+
+
+def phantom_create(desc: dict) -> Phantom:
+    return Phantom(desc)
+
+
+def phantom_rasterize(ph: Phantom, x_true, stream=None):
+    _check(lib().pct_phantom_rasterize(ph.handle, _ptr(x_true), _stream(stream)))
+
+
+class GeometryArgs:
+    """pct_geometry for a workload dict (keeps the angle array alive)."""
+
+    def __init__(self, w: dict, stream_id: int = 0):
+        self.angles = np.ascontiguousarray(w["angles"], dtype=np.float64)
+        m = w["model"]
+        pm = PathModel(m["model"], m.get("chord", W.CHORD_EXACT), m.get("spline_segments", 32),
+                       m.get("noise", W.NOISE_NONE), (C.c_double * 2)(*m["t_range"]),
+                       (C.c_double * 2)(*m.get("v_range", (0.0, 0.0))), m.get("sigma_lat", 0.0),
+                       m.get("sigma_in", 0.0), m.get("sigma_out", 0.0), m.get("rho", 0.0),
+                       m.get("noise_rel", 0.0))
+        self.c = Geometry(self.angles.ctypes.data_as(C.POINTER(C.c_double)), len(self.angles),
+                          int(w["paths_per_angle"]), pm, C.c_uint64(int(w["seed"])),
+                          C.c_uint64(int(stream_id)))
+        self.n_rows = len(self.angles) * int(w["paths_per_angle"])
+
+
+def simulate_workspace_size(ph: Phantom, geo: GeometryArgs, precision: int = PREC_MIXED) -> int:
+    n = C.c_size_t()
+    _check(lib().pct_simulate_workspace_size(ph.handle, C.byref(geo.c), precision, C.byref(n)))
+    return n.value
+
+
+def simulate_count(ph, geo, precision, workspace, row_ptr, stream=None):
+    _check(lib().pct_simulate_count(ph.handle, C.byref(geo.c), precision, _ptr(workspace),
+                                    workspace.numel() * workspace.element_size(), _ptr(row_ptr),
+                                    _stream(stream)))
+
+
+def simulate_fill(ph, geo, precision, workspace, row_ptr, x_true, col, val, b, stream=None):
+    _check(lib().pct_simulate_fill(ph.handle, C.byref(geo.c), precision, _ptr(workspace),
+                                   workspace.numel() * workspace.element_size(), _ptr(row_ptr),
+                                   _ptr(x_true), _ptr(col), _ptr(val), _ptr(b), _stream(stream)))
+
+
+def simulate(ph: Phantom, geo: GeometryArgs, precision: int = PREC_MIXED, stream=None, device="cuda"):
+    """Two-phase simulation into PyTorch-owned buffers; returns a dict of tensors."""
+    import torch
+    ws = torch.empty(simulate_workspace_size(ph, geo, precision), dtype=torch.uint8, device=device)
+    x = torch.empty(ph.nvox, dtype=torch.float32, device=device)
+    rp = torch.empty(geo.n_rows + 1, dtype=torch.int64, device=device)
+    b = torch.empty(max(geo.n_rows, 1), dtype=torch.float32, device=device)[: geo.n_rows]
+    phantom_rasterize(ph, x, stream)
+    simulate_count(ph, geo, precision, ws, rp, stream)
+    nnz = int(rp[-1].item())
+    col = torch.empty(max(nnz, 1), dtype=torch.int32, device=device)
+    val = torch.empty(max(nnz, 1), dtype=torch.float32, device=device)
+    simulate_fill(ph, geo, precision, ws, rp, x, col, val, b, stream)
+    return {"x_true": x, "row_ptr": rp, "col": col[:nnz], "val": val[:nnz], "b": b, "nnz": nnz,
+            "workspace": ws}
+
+
+def simulate_c_alloc(ph: Phantom, geo: GeometryArgs, precision: int = PREC_MIXED, stream=None,
+                     device="cuda"):
+    """pct_simulate(): the library allocates through callbacks (here: torch)."""
+    import torch
+    keep = {}
+
+    def _alloc(nbytes, ctx):
+        t = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+        keep[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def _free(p, ctx):
+        keep.pop(p, None)
+
+    af, ff = ALLOC_FN(_alloc), FREE_FN(_free)
+    out = Csr()
+    _check(lib().pct_simulate(ph.handle, C.byref(geo.c), precision, af, ff, None, C.byref(out),
+                              _stream(stream)))
+
+    def view(p, dtype, n):
+        return keep[p].view(dtype)[:n]
+
+    return {"x_true": view(out.x_true, torch.float32, out.n_cols),
+            "row_ptr": view(out.row_ptr, torch.int64, out.n_rows + 1),
+            "col": view(out.col, torch.int32, out.nnz), "val": view(out.val, torch.float32, out.nnz),
+            "b": view(out.b, torch.float32, out.n_rows), "nnz": out.nnz}
+
+
+def _csr(A):
+    if A is None:
+        return None
+    return C.byref(Csr(A["row_ptr"].numel() - 1, A["x_true"].numel() if "x_true" in A else 0,
+                       A["col"].numel(), A["row_ptr"].data_ptr(), A["col"].data_ptr(),
+                       A["val"].data_ptr(), 0, 0))
+
+
+def forward(ph, geo, A, row0, n_rows, x, y, workspace=None, stream=None):
+    """y = A x over rows [row0, row0 + n_rows) (CSR if A is given, else matrix-free)."""
+    ws = workspace
+    _check(lib().pct_forward(ph.handle if ph else None, C.byref(geo.c) if geo else None, _csr(A),
+                             row0, n_rows, _ptr(x), _ptr(y), _ptr(ws),
+                             0 if ws is None else ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def adjoint(ph, geo, A, row0, n_rows, r, g, workspace=None, stream=None):
+    """g += A^T r over rows [row0, row0 + n_rows)."""
+    ws = workspace
+    _check(lib().pct_adjoint(ph.handle if ph else None, C.byref(geo.c) if geo else None, _csr(A),
+                             row0, n_rows, _ptr(r), _ptr(g), _ptr(ws),
+                             0 if ws is None else ws.numel() * ws.element_size(), _stream(stream)))

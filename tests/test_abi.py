@@ -1,0 +1,82 @@
+"""The C ABI without a GPU: the library builds, exports every function
+include/pct.h declares, and its host-only calls validate arguments."""
+import ctypes as C
+import re
+from pathlib import Path
+
+import pytest
+
+from paper_2108_12369_gb300 import workloads as W
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+@pytest.fixture(scope="module")
+def pct():
+    from paper_2108_12369_gb300 import build, pct as P
+    build.build()
+    return P
+
+
+def declared_functions():
+    names = set()
+    for h in (ROOT / "include").glob("*.h"):
+        text = h.read_text()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(pct_[a-z0-9_]+)\s*\(", text))
+    return sorted(n for n in names if not n.endswith("_fn"))
+
+
+def test_every_declared_function_is_exported(pct):
+    L = pct.lib()
+    names = declared_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(L, n), f"{n} declared in include/ but not exported"
+    assert set(pct.EXPORTS) <= set(names)
+
+
+def test_version(pct):
+    assert "sm_103a" in pct.version()
+
+
+def test_phantom_create_validates(pct):
+    ph = pct.Phantom(W.phantom(2, (200, 200), (1.0, 1.0), skin=False))
+    assert ph.nvox == 40000
+    ph3 = pct.Phantom(W.phantom(3, (20, 30, 40), (1.0, 1.0, 1.0), skin=True))
+    assert ph3.nvox == 24000
+    for bad in ({"dim": 4}, {"n": (0, 10, 1)}, {"h": (1.0, -1.0, 1.0)}, {"raster": 7}, {"kind": 9}):
+        d = dict(W.phantom(2, (10, 10), (1.0, 1.0), skin=False), **bad)
+        with pytest.raises(pct.PctError) as e:
+            pct.Phantom(d)
+        assert e.value.status == pct.EINVAL
+    d = W.phantom(2, (10, 10), (1.0, 1.0), skin=False)
+    d["regions"] = d["regions"] * 4  # 20 > 16 regions
+    with pytest.raises(ValueError):
+        pct.Phantom(d)
+    d = W.phantom(2, (10, 10), (1.0, 1.0), skin=False)
+    d["regions"] = [dict(d["regions"][0], a=(0.0, 1.0, 1.0))]
+    with pytest.raises(pct.PctError):
+        pct.Phantom(d)
+    assert "semi-axis" in pct.last_error()
+
+
+def test_workspace_size_and_geometry_checks(pct):
+    w = W.neo2_2d_spline(n_angles=10, paths_per_angle=100)
+    ph = pct.Phantom(w["phantom"])
+    geo = pct.GeometryArgs(w)
+    for prec in (pct.PREC_MIXED, pct.PREC_F64):
+        n = pct.simulate_workspace_size(ph, geo, prec)
+        assert n >= 10 * 16 + 33 * 32
+    bad_models = [dict(w["model"], model=5), dict(w["model"], spline_segments=0),
+                  dict(w["model"], rho=1.5), dict(w["model"], sigma_lat=-1.0),
+                  dict(w["model"], t_range=(5.0, -5.0)), dict(w["model"], chord=3)]
+    for m in bad_models:
+        g = pct.GeometryArgs(dict(w, model=m))
+        with pytest.raises(pct.PctError) as e:
+            pct.simulate_workspace_size(ph, g, pct.PREC_F64)
+        assert e.value.status == pct.EINVAL
+    with pytest.raises(pct.PctError):
+        pct.simulate_workspace_size(ph, geo, 7)
+    w0 = dict(w, angles=W.angles(0))
+    assert pct.simulate_workspace_size(ph, pct.GeometryArgs(w0), pct.PREC_F64) > 0
