@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark of the pCT simulator hot path on GB300.
+
+One step = one whole simulation of the workload: phantom raster (x_true),
+per-proton path + traversal count, int64 row-pointer scan, nnz read-back,
+and the fill of col / val / b (WEPL with noise), all through the C ABI.
+
+Metric: proton paths per second (whole job), with the CSR bytes per second
+and the fill kernel's achieved HBM bandwidth against the measured peak.
+
+  python bench.py [--gpus N --steps K --warmup W] [--precision mixed|f64]
+                  [--impl ours|reference] [--workload neo2_2d_spline]
+
+Under torchrun (N > 1) every rank simulates its own independent batch of
+protons (generator stream = rank): weak scaling, no collective on the data
+path.  `--impl reference` times the CPU oracle on a bounded sample of the
+same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+from paper_2108_12369_gb300 import workloads as W  # noqa: E402
+
+METRIC = "proton paths/s (CSR generation, whole job)"
+UNIT = "paths/s"
+KERNEL_FILES = {
+    "mixed": ["pct_mixed.cu", "pct_mixed.cuh", "pct_device.cuh"],
+    "f64": ["pct_f64.cu", "pct_device.cuh"],
+}
+FILL_KERNEL = {"mixed": "k_fill_mixed", "f64": "k_fill_f64"}
+# our kernels launched per step: raster, count, 3 scan passes, fill
+LAUNCHES_PER_STEP = {"mixed": 6, "f64": 6}
+
+
+def workload(name: str):
+    return {"neo2_2d_spline": W.neo2_2d_spline, "neo1_2d_straight": W.neo1_2d_straight,
+            "head_3d_spline": W.head_3d_spline}[name]()
+
+
+def peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_hash(prec: str) -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_FILES[prec]:
+        fp = ROOT / "paper_2108_12369_gb300" / "csrc" / f
+        if fp.exists():
+            h.update(fp.read_bytes())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(prec: str, wname: str):
+    """DRAM bytes per fill launch from a committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    p = ROOT / "profiles" / f"{FILL_KERNEL[prec]}_{wname}.json"
+    if not p.exists():
+        return None
+    d = json.loads(p.read_text())
+    if d.get("kernel_hash") != kernel_hash(prec):
+        return None
+    return d.get("traffic_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in Path(self.path).read_text().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(w, target_s: float = 15.0):
+    """The oracle as it stands, all host cores, on a stride sample of the rows."""
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    n_rows = W.n_rows(w)
+    ph = O.Phantom(w["phantom"])
+    t0 = time.perf_counter()
+    x = ph.raster().astype(np.float32)
+    t_raster = time.perf_counter() - t0
+    sim = O.Simulation(ph, x, w["angles"], w["paths_per_angle"], w["model"], w["seed"])
+    # calibrate on a small sample, then size the timed one to ~target_s
+    probe = np.arange(0, n_rows, max(1, n_rows // 2000), dtype=np.int64)
+    t0 = time.perf_counter()
+    sim.rows(probe, threads=cores)
+    rate = len(probe) / max(time.perf_counter() - t0, 1e-6)
+    n_s = int(min(n_rows, max(len(probe), rate * target_s)))
+    rows = np.linspace(0, n_rows - 1, n_s).astype(np.int64)
+    t0 = time.perf_counter()
+    rp, _, _, _, _ = sim.rows(rows, threads=cores)
+    t_rows = time.perf_counter() - t0
+    frac = n_s / n_rows
+    t_total = t_rows + t_raster * frac  # raster prorated to the sample
+    return {"value": n_s / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_s} of {n_rows} rows (even stride) + full raster prorated; "
+                      f"{int(rp[-1])} nonzeros in {t_total:.1f} s",
+            "nnz_per_s": float(rp[-1]) / t_total}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args.workload)
+    from oracle import oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    n_rows = W.n_rows(w)
+    ph = O.Phantom(w["phantom"])
+    per_step = max(1000, int(args.reference_rows))
+    times = []
+    nnz = 0
+    for s in range(args.warmup + args.steps):
+        rows = (np.arange(per_step, dtype=np.int64) * (n_rows // per_step) + s) % n_rows
+        t0 = time.perf_counter()
+        x = ph.raster().astype(np.float32)
+        t_r = time.perf_counter() - t0
+        sim = O.Simulation(ph, x, w["angles"], w["paths_per_angle"], w["model"], w["seed"])
+        t0 = time.perf_counter()
+        rp, _, _, _, _ = sim.rows(rows, threads=cores)
+        t = time.perf_counter() - t0 + t_r * per_step / n_rows
+        if s >= args.warmup:
+            times.append(t)
+            nnz += int(rp[-1])
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": w["name"], "rows": n_rows, "grid": list(w["phantom"]["n"][:w["phantom"]["dim"]]),
+                       "sample_rows_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} of {n_rows} rows per step (even stride), raster prorated"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "nnz_per_s": nnz / total}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2108_12369_gb300 import build as B, pct
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    prec = {"mixed": pct.PREC_MIXED, "f64": pct.PREC_F64}[args.precision]
+    w = workload(args.workload)
+    ph = pct.Phantom(w["phantom"])
+    geo = pct.GeometryArgs(w, stream_id=rank)
+    n_rows = geo.n_rows
+    ws = torch.empty(pct.simulate_workspace_size(ph, geo, prec), dtype=torch.uint8, device=dev)
+    x = torch.empty(ph.nvox, dtype=torch.float32, device=dev)
+    rp = torch.empty(n_rows + 1, dtype=torch.int64, device=dev)
+    b = torch.empty(n_rows, dtype=torch.float32, device=dev)
+    pct.phantom_rasterize(ph, x)
+    pct.simulate_count(ph, geo, prec, ws, rp)
+    nnz = int(rp[-1].item())
+    col = torch.empty(nnz, dtype=torch.int32, device=dev)
+    val = torch.empty(nnz, dtype=torch.float32, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        pct.phantom_rasterize(ph, x)
+        pct.simulate_count(ph, geo, prec, ws, rp)
+        n = int(rp[-1].item())  # nnz read-back sizes the fill, as a caller must
+        if n != nnz:
+            raise RuntimeError("nnz changed between steps")
+        if ev:
+            ev[1].record(stream)
+        pct.simulate_fill(ph, geo, prec, ws, rp, x, col, val, b)
+        if ev:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for s in range(args.steps):
+        step(evs[s])
+        flush.zero_()  # L2 flush between steps, outside the step's events
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
+    fill_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * n_rows * args.steps / total_s
+
+    # end to end through the C ABI with host buffers: angle / basis tables go
+    # up from host memory inside every call, the CSR + b come back to pinned
+    # host memory every step
+    h_rp = torch.empty(n_rows + 1, dtype=torch.int64, pin_memory=True)
+    h_col = torch.empty(nnz, dtype=torch.int32, pin_memory=True)
+    h_val = torch.empty(nnz, dtype=torch.float32, pin_memory=True)
+    h_b = torch.empty(n_rows, dtype=torch.float32, pin_memory=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        step()
+        h_rp.copy_(rp, non_blocking=True)
+        h_col.copy_(col, non_blocking=True)
+        h_val.copy_(val, non_blocking=True)
+        h_b.copy_(b, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * n_rows * e2e_steps / e2e_s
+    K = w["model"].get("spline_segments", 1)
+    h2d = len(w["angles"]) * 16 + (K + 1) * 32
+    d2h = (n_rows + 1) * 8 + nnz * 8 + n_rows * 4
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = peaks()
+    alg_bytes = 8.0 * nnz + 12.0 * n_rows  # col + val per nonzero; row_ptr read + b write per row
+    fill_avg_s = statistics.mean(fill_ms) / 1e3
+    achieved = alg_bytes / fill_avg_s / 1e9
+    traffic = recorded_traffic(args.precision, w["name"])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "mixed" else "f64", "precision": args.precision,
+        "data": "synthetic",
+        "config": {"workload": w["name"], "grid": list(w["phantom"]["n"][:w["phantom"]["dim"]]),
+                   "voxel_mm": w["phantom"]["h"][0], "angles": len(w["angles"]),
+                   "paths_per_angle": w["paths_per_angle"], "rows_per_gpu": n_rows, "nnz_per_gpu": nnz,
+                   "path_model": "spline" if w["model"]["model"] == W.SPLINE else "straight",
+                   "spline_segments": K, "noise_rel": w["model"].get("noise_rel", 0.0),
+                   "l2": "512 MB write between steps (untimed); outputs per step >> L2",
+                   "parallelism": f"independent protons per GPU x{world}"},
+        "csr_gbs": (8.0 * nnz + 12.0 * n_rows) * world * args.steps / total_s / 1e9,
+        "nnz_per_s": world * nnz * args.steps / total_s,
+        "roofline": {"bound": "hbm", "kernel": FILL_KERNEL[args.precision], "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": f"{peak_kind} hbm_gbs (copy, burst)",
+                     "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
+                     "fill_ms": statistics.mean(fill_ms)},
+        "phase_ms": {"raster_count_scan_readback": statistics.mean(
+            [e[0].elapsed_time(e[1]) for e in evs]), "fill": statistics.mean(fill_ms)},
+        "wall_s_timed_loop": t_wall,
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
+        "gpu_launches": LAUNCHES_PER_STEP[args.precision] * args.steps,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "f64"], default="mixed")
+    ap.add_argument("--workload", default="neo2_2d_spline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--reference-rows", type=int, default=60000)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

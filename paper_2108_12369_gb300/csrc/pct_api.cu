@@ -130,7 +130,7 @@ extern "C" pct_status pct_phantom_rasterize(const pct_phantom* ph, float* x, voi
 namespace {
 
 struct Layout {
-  size_t cs, basis, partial, rec, total;
+  size_t cs, basis, basis32, partial, rec, total;
   long long rows;
   int K;
 };
@@ -171,9 +171,12 @@ Layout layout_of(const pct_phantom*, const pct_geometry* g, int precision) {
   off = align256(off + sizeof(double2) * (size_t)(g->n_angles > 0 ? g->n_angles : 1));
   L.basis = off;
   off = align256(off + sizeof(Basis4) * (size_t)(L.K + 1));
+  L.basis32 = off;
+  off = align256(off + basis_df_bytes(L.K + 1));
   L.partial = off;
   off = align256(off + sizeof(long long) * (size_t)scan_partials_needed(L.rows));
   L.rec = off;
+  if (precision == PCT_PREC_MIXED) off = align256(off + mixed_record_size(L.rows));
   L.total = off;
   return L;
 }
@@ -232,9 +235,18 @@ pct_status make_sim(const pct_phantom* ph, const pct_geometry* g, int precision,
     bs[j].h01 = 3.0 * s2 - 2.0 * s3;
     bs[j].h11 = s3 - s2;
   }
+  std::vector<double> sj((size_t)L.K + 1), h10((size_t)L.K + 1), h11((size_t)L.K + 1);
+  for (int j = 0; j <= L.K; ++j) {
+    sj[j] = (double)j / (double)L.K;
+    h10[j] = bs[j].h10;
+    h11[j] = bs[j].h11;
+  }
+  std::vector<char> bf(basis_df_bytes(L.K + 1));
+  fill_basis_df(sj.data(), h10.data(), h11.data(), L.K + 1, bf.data());
   // the host vectors are pageable: the copies return once they are staged
   if (cudaMemcpyAsync(base + L.cs, cs.data(), sizeof(double2) * cs.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(base + L.basis, bs.data(), sizeof(Basis4) * bs.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      cudaMemcpyAsync(base + L.basis, bs.data(), sizeof(Basis4) * bs.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(base + L.basis32, bf.data(), bf.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return cuda_check("table upload");
   return PCT_OK;
 }
@@ -259,8 +271,10 @@ extern "C" pct_status pct_simulate_count(const pct_phantom* ph, const pct_geomet
   if (rc != PCT_OK) return rc;
   if (!row_ptr) return fail(PCT_EINVAL, "row_ptr is NULL");
   long long* rp = (long long*)row_ptr;
-  if (precision != PCT_PREC_F64) return fail(PCT_EUNSUPPORTED, "the mixed form is not built yet");
-  launch_count_f64(S, 0, L.rows, rp + 1, st);
+  if (precision == PCT_PREC_F64)
+    launch_count_f64(S, 0, L.rows, rp + 1, st);
+  else
+    launch_count_mixed(S, (const char*)ws + L.basis32, L.rows, (char*)ws + L.rec, rp + 1, st);
   if ((rc = cuda_check("count launch")) != PCT_OK) return rc;
   launch_scan_rowptr(rp, L.rows, (long long*)((char*)ws + L.partial), st);
   return cuda_check("scan launch");
@@ -276,8 +290,11 @@ extern "C" pct_status pct_simulate_fill(const pct_phantom* ph, const pct_geometr
   if (rc != PCT_OK) return rc;
   if (L.rows > 0 && (!row_ptr || !x || !b)) return fail(PCT_EINVAL, "NULL row_ptr, x_true or b");
   const long long* rp = (const long long*)row_ptr;
-  if (precision != PCT_PREC_F64) return fail(PCT_EUNSUPPORTED, "the mixed form is not built yet");
-  launch_fill_f64(S, 0, L.rows, rp, x, (int*)col, val, b, st);
+  if (precision == PCT_PREC_F64)
+    launch_fill_f64(S, 0, L.rows, rp, x, (int*)col, val, b, st);
+  else
+    launch_fill_mixed(S, (const char*)ws + L.basis32, L.rows, (const char*)ws + L.rec, rp, x, (int*)col, val, b,
+                      st);
   return cuda_check("fill launch");
 }
 

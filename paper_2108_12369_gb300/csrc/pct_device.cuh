@@ -116,7 +116,12 @@ struct UniformStream {
       buf = philox4x64_10(row, (unsigned long long)b, 0ULL, 0ULL, k0, k1);
       block = b;
     }
-    return word_to_uniform(buf.w[j & 3]);
+    const int w = (int)(j & 3);
+    unsigned long long x = buf.w[0];
+    x = (w == 1) ? buf.w[1] : x;
+    x = (w == 2) ? buf.w[2] : x;
+    x = (w == 3) ? buf.w[3] : x;
+    return word_to_uniform(x);
   }
 };
 
@@ -182,7 +187,9 @@ __device__ __forceinline__ bool hull_hit(const PhantomDev& ph, const double A[3]
                                          const double g[3], double& lam_in, double& lam_out) {
   int axes = (ph.g.dim == 3 && ph.kind == PCT_ELLIPSOID) ? 3 : 2;
   double alpha = 0.0, beta = 0.0, gamma = 0.0;
-  for (int a = 0; a < axes; ++a) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a >= axes) break;
     double e = g[a] * ph.ra[0][a];
     double f = (A[a] - ph.c[0][a]) * ph.ra[0][a];
     alpha = alpha + e * e;
@@ -282,7 +289,9 @@ __device__ __forceinline__ PathF64 path_setup(const SimDev& S, long long row) {
   }
   if (md.model == PCT_PATH_SPLINE) {
     double l = 0.0;
-    for (int a = 0; a < dim; ++a) l = l + (p.P1[a] - p.P0[a]) * p.g0[a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (a < dim) l = l + (p.P1[a] - p.P0[a]) * p.g0[a];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       p.m0[a] = l * p.g0[a];
@@ -400,7 +409,9 @@ __device__ __forceinline__ bool seg_setup_f64(const GridDev& g, const double P[3
     sg.idx[a] = 0;
     sg.D[a] = 0.0;
   }
-  for (int a = 0; a < dim; ++a) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a >= dim) break;
     sg.D[a] = Q[a] - P[a];
     if (sg.D[a] == 0.0) {
       double fl = floor((P[a] - g.o[a]) / g.h[a]);
@@ -421,10 +432,14 @@ __device__ __forceinline__ bool seg_setup_f64(const GridDev& g, const double P[3
   }
   if (!(sg.s_in < sg.s_out)) return false;
   double len2 = 0.0;
-  for (int a = 0; a < dim; ++a) len2 = len2 + sg.D[a] * sg.D[a];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (a < dim) len2 = len2 + sg.D[a] * sg.D[a];
   sg.seglen = sqrt(len2);
   // start voxel: (planes with sigma <= s_in) - 1, or n - that count
-  for (int a = 0; a < dim; ++a) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a >= dim) break;
     if (!sg.act[a]) continue;
     const int n = g.n[a];
     double x = P[a] + sg.s_in * sg.D[a];
@@ -459,14 +474,16 @@ __device__ __forceinline__ void seg_walk_f64(const GridDev& g, SegF64& sg, Merge
   while (guard-- > 0) {
     double s_next = sg.s_out;
     double sa[3];
-    for (int a = 0; a < dim; ++a) {
-      sa[a] = sg.act[a] ? sigma_at(sg, a, sg.kn[a]) : 2.0;
-      if (sg.act[a] && sa[a] < s_next) s_next = sa[a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      sa[a] = (a < dim && sg.act[a]) ? sigma_at(sg, a, sg.kn[a]) : 2.0;
+      if (a < dim && sg.act[a] && sa[a] < s_next) s_next = sa[a];
     }
     mg.emit(vox_col(g, sg.idx), sg.seglen * (s_next - s_prev), sink);
     if (!(s_next < sg.s_out)) break;
-    for (int a = 0; a < dim; ++a) {
-      if (sg.act[a] && sa[a] == s_next) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a < dim && sg.act[a] && sa[a] == s_next) {
         sg.idx[a] += sg.step[a];
         sg.kn[a] += sg.step[a];
       }

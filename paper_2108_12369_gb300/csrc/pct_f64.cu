@@ -18,7 +18,9 @@ __device__ __forceinline__ double rsp_at(const PhantomDev& ph, const double p[3]
   double v = 0.0;
   for (int r = 0; r < ph.n_regions; ++r) {
     double q = 0.0;
-    for (int a = 0; a < axes; ++a) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a >= axes) break;
       double d = (p[a] - ph.c[r][a]) / ph.a[r][a];
       q = q + d * d;
     }
@@ -39,13 +41,17 @@ __global__ void k_raster(PhantomDev ph, float* __restrict__ x, long long nvox) {
   double p[3] = {0.0, 0.0, 0.0};
   double val;
   if (ph.raster == PCT_RASTER_CENTER) {
-    for (int a = 0; a < g.dim; ++a) p[a] = g.o[a] + ((double)idx[a] + 0.5) * g.h[a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (a < g.dim) p[a] = g.o[a] + ((double)idx[a] + 0.5) * g.h[a];
     val = rsp_at(ph, p);
   } else {
     int nc = (g.dim == 3) ? 8 : 4;
     double sum = 0.0;
     for (int c = 0; c < nc; ++c) {
-      for (int a = 0; a < g.dim; ++a) p[a] = g.o[a] + (double)(idx[a] + ((c >> a) & 1)) * g.h[a];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (a < g.dim) p[a] = g.o[a] + (double)(idx[a] + ((c >> a) & 1)) * g.h[a];
       sum = sum + rsp_at(ph, p);
     }
     val = sum * (1.0 / (double)nc);

@@ -18,6 +18,17 @@ void launch_mf_forward_f64(const SimDev& S, long long row0, long long n, const f
 void launch_mf_adjoint_f64(const SimDev& S, long long row0, long long n, const float* r, float* g,
                            cudaStream_t st);
 
+// double-float certified form (pct_mixed.cu).  rec: per-row records
+// (mixed_record_size bytes); tab: Hermite basis table (basis_df_bytes(K + 1)
+// bytes, filled on the host by fill_basis_df from s, h10, h11 at j = 0..K).
+size_t mixed_record_size(long long rows);
+size_t basis_df_bytes(int n);
+void fill_basis_df(const double* s, const double* h10, const double* h11, int n, void* host_out);
+void launch_count_mixed(const SimDev& S, const void* tab, long long n, void* rec, long long* counts,
+                        cudaStream_t st);
+void launch_fill_mixed(const SimDev& S, const void* tab, long long n, const void* rec, const long long* row_ptr,
+                       const float* x, int* col, float* val, float* b, cudaStream_t st);
+
 // row pointers (pct_scan.cu): row_ptr[0] = 0, row_ptr[1..n] = inclusive scan
 // of the counts already stored in row_ptr[1..n]; partial holds
 // ceil(n / kScanTile) + 1 int64 of scratch.
