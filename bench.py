@@ -48,9 +48,15 @@ FILL_KERNEL = {"mixed": "k_fill_mixed", "f64": "k_fill_f64"}
 LAUNCHES_PER_STEP = {"mixed": 6, "f64": 6}
 
 
-def workload(name: str):
-    return {"neo2_2d_spline": W.neo2_2d_spline, "neo1_2d_straight": W.neo1_2d_straight,
-            "head_3d_spline": W.head_3d_spline}[name]()
+def workload(name: str, angles: int = 0, paths_per_angle: int = 0):
+    """The named workload; angles / paths_per_angle > 0 shrink it (profiling)."""
+    w = {"neo2_2d_spline": W.neo2_2d_spline, "neo1_2d_straight": W.neo1_2d_straight,
+         "head_3d_spline": W.head_3d_spline}[name]()
+    if angles > 0:
+        w["angles"] = W.angles(angles)
+    if paths_per_angle > 0:
+        w["paths_per_angle"] = paths_per_angle
+    return w
 
 
 def peaks():
@@ -163,7 +169,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = workload(args.workload)
+    w = workload(args.workload, args.angles, args.paths_per_angle)
     from oracle import oracle as O
     O.build()
     cores = os.cpu_count() or 1
@@ -219,7 +225,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     prec = {"mixed": pct.PREC_MIXED, "f64": pct.PREC_F64}[args.precision]
-    w = workload(args.workload)
+    w = workload(args.workload, args.angles, args.paths_per_angle)
     ph = pct.Phantom(w["phantom"])
     geo = pct.GeometryArgs(w, stream_id=rank)
     n_rows = geo.n_rows
@@ -361,6 +367,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--reference-rows", type=int, default=60000)
+    ap.add_argument("--angles", type=int, default=0, help="override the angle count (profiling)")
+    ap.add_argument("--paths-per-angle", type=int, default=0, help="override protons per angle (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -130,7 +130,7 @@ extern "C" pct_status pct_phantom_rasterize(const pct_phantom* ph, float* x, voi
 namespace {
 
 struct Layout {
-  size_t cs, basis, basis32, partial, rec, total;
+  size_t cs, basis, basis32, partial, args, rec, total;
   long long rows;
   int K;
 };
@@ -175,6 +175,8 @@ Layout layout_of(const pct_phantom*, const pct_geometry* g, int precision) {
   off = align256(off + basis_df_bytes(L.K + 1));
   L.partial = off;
   off = align256(off + sizeof(long long) * (size_t)scan_partials_needed(L.rows));
+  L.args = off;
+  off = align256(off + mixed_args_bytes());
   L.rec = off;
   if (precision == PCT_PREC_MIXED) off = align256(off + mixed_record_size(L.rows));
   L.total = off;
@@ -274,7 +276,7 @@ extern "C" pct_status pct_simulate_count(const pct_phantom* ph, const pct_geomet
   if (precision == PCT_PREC_F64)
     launch_count_f64(S, 0, L.rows, rp + 1, st);
   else
-    launch_count_mixed(S, (const char*)ws + L.basis32, L.rows, (char*)ws + L.rec, rp + 1, st);
+    launch_count_mixed(S, (const char*)ws + L.basis32, L.rows, (char*)ws + L.rec, rp + 1, (char*)ws + L.args, st);
   if ((rc = cuda_check("count launch")) != PCT_OK) return rc;
   launch_scan_rowptr(rp, L.rows, (long long*)((char*)ws + L.partial), st);
   return cuda_check("scan launch");
@@ -294,7 +296,7 @@ extern "C" pct_status pct_simulate_fill(const pct_phantom* ph, const pct_geometr
     launch_fill_f64(S, 0, L.rows, rp, x, (int*)col, val, b, st);
   else
     launch_fill_mixed(S, (const char*)ws + L.basis32, L.rows, (const char*)ws + L.rec, rp, x, (int*)col, val, b,
-                      st);
+                      (char*)ws + L.args, st);
   return cuda_check("fill launch");
 }
 

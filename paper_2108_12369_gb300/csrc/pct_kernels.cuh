@@ -22,12 +22,14 @@ void launch_mf_adjoint_f64(const SimDev& S, long long row0, long long n, const f
 // (mixed_record_size bytes); tab: Hermite basis table (basis_df_bytes(K + 1)
 // bytes, filled on the host by fill_basis_df from s, h10, h11 at j = 0..K).
 size_t mixed_record_size(long long rows);
+size_t mixed_args_bytes();
 size_t basis_df_bytes(int n);
 void fill_basis_df(const double* s, const double* h10, const double* h11, int n, void* host_out);
-void launch_count_mixed(const SimDev& S, const void* tab, long long n, void* rec, long long* counts,
+// args: mixed_args_bytes() of workspace for a global copy of the arguments
+void launch_count_mixed(const SimDev& S, const void* tab, long long n, void* rec, long long* counts, void* args,
                         cudaStream_t st);
 void launch_fill_mixed(const SimDev& S, const void* tab, long long n, const void* rec, const long long* row_ptr,
-                       const float* x, int* col, float* val, float* b, cudaStream_t st);
+                       const float* x, int* col, float* val, float* b, void* args, cudaStream_t st);
 
 // row pointers (pct_scan.cu): row_ptr[0] = 0, row_ptr[1..n] = inclusive scan
 // of the counts already stored in row_ptr[1..n]; partial holds

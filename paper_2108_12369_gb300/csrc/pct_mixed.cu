@@ -17,17 +17,6 @@ struct MixArgs {
   PathF64* r64;         // [rows]
 };
 
-// exact endpoints of segment q of a path (for the on-demand FP64 decisions)
-struct EndsF64 {
-  const SimDev* S;
-  const PathF64* p;
-  int q;
-  __device__ void operator()(double P[3], double Q[3]) const {
-    path_vertex(*S, *p, q, P);
-    path_vertex(*S, *p, q + 1, Q);
-  }
-};
-
 // feeds FP64-walked entries into the FP32 row merge
 template <class M>
 struct MergeToF32 {
@@ -38,6 +27,10 @@ struct MergeToF32 {
   }
 };
 
+// Finished entries of a row.  The count kernel only counts them.  The fill
+// kernel stages them per lane in shared memory ([k][33] layout: lanes write
+// and read conflict-free) and the warp writes each lane's run with
+// coalesced stores; segments walked in FP64 write straight to global.
 struct CountSinkM {
   long long n;
   template <class L>
@@ -46,85 +39,212 @@ struct CountSinkM {
   }
 };
 
-struct FillSinkM {
+constexpr int kChunk = 32;     // walk steps between two flushes
+constexpr int kRingPitch = 33;
+
+struct FillSinkR {
+  int* colb;        // this warp's staging, [kChunk][kRingPitch]
+  float* valb;
+  int n, lane;      // staged entries of this lane
   int* col;
   float* val;
+  long long pos;    // next global position of this lane's row
+  bool direct;
   const float* x;
-  long long pos;
   float sum, comp;  // Kahan-compensated WEPL
   bool constant;
   float hconst;
   __device__ void put(int c, float len) {
-    col[pos] = c;
-    val[pos] = constant ? hconst : len;
-    ++pos;
+    const float v = constant ? hconst : len;
+    if (direct) {
+      col[pos] = c;
+      val[pos] = v;
+      ++pos;
+    } else {
+      colb[n * kRingPitch + lane] = c;
+      valb[n * kRingPitch + lane] = v;
+      ++n;
+    }
     float y = len * __ldg(x + c) - comp;
     float t = sum + y;
     comp = (t - sum) - y;
     sum = t;
   }
+  // warp-cooperative: every lane's staged run goes to its row
+  __device__ void flush() {
+    unsigned todo = __ballot_sync(0xffffffffu, n > 0);
+    while (todo) {
+      const int L = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int nL = __shfl_sync(0xffffffffu, n, L);
+      const long long pL = __shfl_sync(0xffffffffu, pos, L);
+      if (lane < nL) {
+        col[pL + lane] = colb[lane * kRingPitch + L];
+        val[pL + lane] = valb[lane * kRingPitch + L];
+      }
+    }
+    pos += n;
+    n = 0;
+    __syncwarp();
+  }
 };
 
-// all segments of one row; kLengths selects fill (true) or count (false)
-template <int DIM, bool kLengths, class Sink>
-__device__ __forceinline__ void walk_row_df(const SimDev& S, const MixArgs& M, const RowDF& r, const PathF64* p64,
-                                            Sink& sink) {
+// all segments of one row.  The segment loop runs to the warp's largest
+// vertex count so that the lanes set up segment q together; walks advance
+// in chunks of kChunk entries, after which the fill kernel flushes.
+template <int DIM, bool kFill, class Sink>
+__device__ __forceinline__ void walk_row_df(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
+                                            const RowDF& r, const PathF64* p64, bool live_row, Sink& sink) {
+  // r refers to the row record in global memory: its fields are re-read per
+  // segment (L1 hits) instead of occupying ~40 registers for the whole row
   const GridDev& g = S.ph.g;
+  const float mag = live_row ? r.mag : 0.f;
   RowMerge<float> mg;
   mg.init();
   MergeToF32<RowMerge<float>> m64{&mg};
+  const int nv = live_row ? r.nv : 0;
+  const int nv_max = __reduce_max_sync(0xffffffffu, nv);
   df Va[3], Vb[3];
-  vertex_df<DIM>(r, M.tab, M.R, 0, Va);
-  for (int q = 0; q + 1 < r.nv; ++q) {
-    vertex_df<DIM>(r, M.tab, M.R, q + 1, Vb);
-    mg.seg_begin();
+  if (nv > 0) vertex_df<DIM>(r, M.tab, M.R, 0, Va);
+  for (int q = 0; q + 1 < nv_max; ++q) {
+    const bool act = q + 1 < nv;
+    int res = 0;
     SegDF sg;
-    EndsF64 ends{&S, p64, q};
-    int res = seg_setup_df<DIM>(g, M.gd, Va, Vb, r.mag, sg, ends);
-    if (res == 1) {
-      walk_df<DIM, kLengths>(g, sg, mg, sink, ends);
-    } else if (res == 2) {
-      double P[3], Q[3];
-      ends(P, Q);
-      SegF64 s64;
-      if (seg_setup_f64(g, P, Q, s64)) seg_walk_f64(g, s64, m64, sink);
+    Walk32 w;
+    ExactRef ends{Sg, p64, q};
+    if (act) {
+      vertex_df<DIM>(r, M.tab, M.R, q + 1, Vb);
+      mg.seg_begin();
+      res = 1;
+      if (!seg_setup_fast<DIM>(g, M.gd, Va, Vb, mag, sg, w)) {
+        res = seg_setup_df<DIM>(g, M.gd, Va, Vb, mag, sg, ends);
+        if (res == 1) walk_from_df<DIM>(sg, w);
+      }
     }
-    mg.seg_end();
+    // segments whose direction cannot be certified are walked in FP64
+    const bool f64seg = act && res == 2;
+    if (__any_sync(0xffffffffu, f64seg)) {
+      if constexpr (kFill) sink.flush();
+      if (f64seg) {
+        if constexpr (kFill) sink.direct = true;
+        double P[3], Q[3];
+        path_vertex(*Sg, *p64, q, P);
+        path_vertex(*Sg, *p64, q + 1, Q);
+        SegF64 s64;
+        if (seg_setup_f64(g, P, Q, s64)) seg_walk_f64(g, s64, m64, sink);
+        if constexpr (kFill) sink.direct = false;
+      }
+    }
+    const bool walking = act && res == 1;
+    Lean<DIM> L;
+    const float seglen = sg.L;
+    if (walking) lean_begin<DIM>(g, sg, w, q, L);
+    if constexpr (kFill) {
+      while (__any_sync(0xffffffffu, walking && !L.done)) {
+#pragma unroll 1
+        for (int c = 0; c < kChunk; ++c) {
+          if (walking && !L.done) {
+            const int vc = L.col;
+            const float l = lean_step<DIM>(L, r, M.tab, M.R, M.gd, g, mag, ends);
+            mg.emit(vc, l * seglen, sink);
+          }
+        }
+        sink.flush();
+      }
+    } else {
+      if (walking) {
+        while (!L.done) {
+          const int vc = L.col;
+          lean_step<DIM>(L, r, M.tab, M.R, M.gd, g, mag, ends);
+          mg.emit(vc, 0.f, sink);
+        }
+      }
+    }
+    if (act) {
+      mg.seg_end();
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) Va[a] = Vb[a];
+      for (int a = 0; a < DIM; ++a) Va[a] = Vb[a];
+    }
   }
-  mg.finish(sink);
+  if (nv > 0) mg.finish(sink);
+  if constexpr (kFill) sink.flush();
 }
 
+// Rows of one block are regrouped by vertex count (path kind) so that each
+// warp walks rows with the same number of segments.  Returns the row this
+// thread processes (or -1).  key: 0, 1, 2 for 2, 4, more vertices.
+__device__ __forceinline__ long long regroup_rows(long long row, int key) {
+  __shared__ int cnt[3];
+  __shared__ int perm[128];
+  if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  int slot = -1;
+  if (key >= 0) slot = atomicAdd(&cnt[key], 1);
+  __syncthreads();
+  if (key >= 0) {
+    int base = (key > 0 ? cnt[0] : 0) + (key > 1 ? cnt[1] : 0);
+    perm[base + slot] = threadIdx.x;
+  }
+  int total = cnt[0] + cnt[1] + cnt[2];
+  __syncthreads();
+  long long block0 = row - threadIdx.x;
+  return (threadIdx.x < total) ? block0 + perm[threadIdx.x] : -1;
+}
+
+__device__ __forceinline__ int nv_key(int nv) { return nv <= 2 ? 0 : (nv <= 4 ? 1 : 2); }
+
 template <int DIM>
-__global__ void __launch_bounds__(128) k_count_mixed(SimDev S, MixArgs M, long long n,
-                                                     long long* __restrict__ counts) {
+__global__ void __launch_bounds__(128) k_count_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
+                                                     long long n, long long* __restrict__ counts) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  RowDF r;
-  {
+  int key = -1;
+  if (i < n) {
     PathF64 p = path_setup(S, i);
     M.r64[i] = p;  // exact decisions read the FP64 path back from here
     float fac = (S.md.noise == PCT_NOISE_GAUSS_REL) ? (float)(1.0 + S.md.noise_rel * p.z_noise) : 1.0f;
+    RowDF r;
     make_rowdf<DIM>(p, S.R, fac, r);
+    M.rdf[i] = r;
+    key = nv_key(p.nv);
   }
-  M.rdf[i] = r;
+  __threadfence_block();
+  long long row = regroup_rows(i, key);
+  const bool live = row >= 0;
   CountSinkM cs{0};
-  walk_row_df<DIM, false>(S, M, r, M.r64 + i, cs);
-  counts[i] = cs.n;
+  walk_row_df<DIM, false>(S, M, Sg, gdg, M.rdf[live ? row : 0], M.r64 + (live ? row : 0), live, cs);
+  if (live) counts[row] = cs.n;
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(128) k_fill_mixed(SimDev S, MixArgs M, long long n,
+__global__ void __launch_bounds__(128) k_fill_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
+                                                    long long n,
                                                     const long long* __restrict__ row_ptr,
                                                     const float* __restrict__ x, int* __restrict__ col,
                                                     float* __restrict__ val, float* __restrict__ b) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const RowDF r = M.rdf[i];
-  FillSinkM fs{col, val, x, row_ptr[i], 0.f, 0.f, S.md.chord == PCT_CHORD_CONSTANT, (float)S.ph.g.h[0]};
-  walk_row_df<DIM, true>(S, M, r, M.r64 + i, fs);
-  b[i] = fs.sum * r.fac;
+  int key = (i < n) ? nv_key(M.rdf[i].nv) : -1;
+  long long row = regroup_rows(i, key);
+  const bool live = row >= 0;
+  const RowDF& r = M.rdf[live ? row : 0];
+  __shared__ int colb[4][kChunk * kRingPitch];
+  __shared__ float valb[4][kChunk * kRingPitch];
+  const int wid = threadIdx.x >> 5;
+  FillSinkR fs;
+  fs.colb = colb[wid];
+  fs.valb = valb[wid];
+  fs.n = 0;
+  fs.lane = threadIdx.x & 31;
+  fs.col = col;
+  fs.val = val;
+  fs.pos = live ? row_ptr[row] : 0;
+  fs.direct = false;
+  fs.x = x;
+  fs.sum = 0.f;
+  fs.comp = 0.f;
+  fs.constant = S.md.chord == PCT_CHORD_CONSTANT;
+  fs.hconst = (float)S.ph.g.h[0];
+  walk_row_df<DIM, true>(S, M, Sg, gdg, r, M.r64 + (live ? row : 0), live, fs);
+  if (live) b[row] = fs.sum * r.fac;
 }
 
 static df split_host(double v) {
@@ -160,28 +280,48 @@ void fill_basis_df(const double* s, const double* h10, const double* h11, int n,
 
 size_t basis_df_bytes(int n) { return sizeof(BasisDF) * (size_t)n; }
 
-void launch_count_mixed(const SimDev& S, const void* tab, long long n, void* rec, long long* counts,
+size_t mixed_args_bytes() { return ((sizeof(SimDev) + 255) & ~(size_t)255) + sizeof(GridDF); }
+
+// the kernel arguments, also copied to global memory for the out-of-line
+// exact comparisons (the copies are staged before cudaMemcpyAsync returns)
+static bool upload_args(const SimDev& S, const MixArgs& M, void* args, cudaStream_t st, const SimDev** Sg,
+                        const GridDF** gdg) {
+  char* base = (char*)args;
+  size_t off = (sizeof(SimDev) + 255) & ~(size_t)255;
+  *Sg = (const SimDev*)base;
+  *gdg = (const GridDF*)(base + off);
+  return cudaMemcpyAsync(base, &S, sizeof(SimDev), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+         cudaMemcpyAsync(base + off, &M.gd, sizeof(GridDF), cudaMemcpyHostToDevice, st) == cudaSuccess;
+}
+
+void launch_count_mixed(const SimDev& S, const void* tab, long long n, void* rec, long long* counts, void* args,
                         cudaStream_t st) {
   if (n <= 0) return;
   MixArgs M = mix_args(S, n, tab, rec);
+  const SimDev* Sg;
+  const GridDF* gdg;
+  if (!upload_args(S, M, args, st, &Sg, &gdg)) return;
   int threads = 128;
   unsigned blocks = (unsigned)((n + threads - 1) / threads);
   if (S.ph.g.dim == 2)
-    k_count_mixed<2><<<blocks, threads, 0, st>>>(S, M, n, counts);
+    k_count_mixed<2><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n, counts);
   else
-    k_count_mixed<3><<<blocks, threads, 0, st>>>(S, M, n, counts);
+    k_count_mixed<3><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n, counts);
 }
 
 void launch_fill_mixed(const SimDev& S, const void* tab, long long n, const void* rec, const long long* row_ptr,
-                       const float* x, int* col, float* val, float* b, cudaStream_t st) {
+                       const float* x, int* col, float* val, float* b, void* args, cudaStream_t st) {
   if (n <= 0) return;
   MixArgs M = mix_args(S, n, tab, (void*)rec);
+  const SimDev* Sg;
+  const GridDF* gdg;
+  if (!upload_args(S, M, args, st, &Sg, &gdg)) return;
   int threads = 128;
   unsigned blocks = (unsigned)((n + threads - 1) / threads);
   if (S.ph.g.dim == 2)
-    k_fill_mixed<2><<<blocks, threads, 0, st>>>(S, M, n, row_ptr, x, col, val, b);
+    k_fill_mixed<2><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n, row_ptr, x, col, val, b);
   else
-    k_fill_mixed<3><<<blocks, threads, 0, st>>>(S, M, n, row_ptr, x, col, val, b);
+    k_fill_mixed<3><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n, row_ptr, x, col, val, b);
 }
 
 size_t mixed_record_size(long long rows) {

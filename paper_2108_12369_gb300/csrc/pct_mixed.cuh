@@ -131,8 +131,8 @@ struct GridDF {
   float of[3], rh[3];
 };
 
-template <int DIM, class T>
-__device__ __forceinline__ T pick(const T (&v)[3], int ax) {
+template <int DIM, class T, int N>
+__device__ __forceinline__ T pick(const T (&v)[N], int ax) {
   T r = v[0];
 #pragma unroll
   for (int a = 1; a < DIM; ++a)
@@ -212,6 +212,7 @@ struct Ev {
 
 struct SegDF {
   df P[3];       // start vertex
+  df D[3];       // Q - P
   df inv[3];     // 1 / D
   df dl[3];      // h / D
   df sn[3];      // sigma of each axis' next plane
@@ -220,10 +221,36 @@ struct SegDF {
   int idx[3], kn[3], step[3];
   Ev in, out;
   df s_in, s_out;
-  // exact data, built on demand
-  bool have_ex;
-  double ex_dl[3], ex_s0[3];
 };
+
+// Where the FP64 definition of a segment can be rebuilt: kernel arguments
+// (a copy in global memory), the row's FP64 path record, the segment index.
+struct ExactRef {
+  const SimDev* S;
+  const PathF64* p;
+  int q;
+};
+
+// sigma of plane k of axis a in the FP64 definition
+__device__ __forceinline__ double sigma_f64(const GridDev& g, const double P[3], const double Q[3], int a, int k) {
+  double D = Q[a] - P[a];
+  double inv = 1.0 / D;
+  double dl = g.h[a] * inv;
+  double s0 = (g.o[a] - P[a]) * inv;
+  return fma((double)k, dl, s0);
+}
+
+// exact sign of sigma(e1) - sigma(e2) from the FP64 definition (rare: only
+// where the double-float bounds cannot decide, in practice exact ties)
+__device__ __noinline__ int exact_cmp(ExactRef ref, int ax1, int k1, int ax2, int k2) {
+  const SimDev& S = *ref.S;
+  double P[3], Q[3];
+  path_vertex(S, *ref.p, ref.q, P);
+  path_vertex(S, *ref.p, ref.q + 1, Q);
+  double x1 = ax1 < 0 ? (double)k1 : sigma_f64(S.ph.g, P, Q, ax1, k1);
+  double x2 = ax2 < 0 ? (double)k2 : sigma_f64(S.ph.g, P, Q, ax2, k2);
+  return x1 < x2 ? -1 : (x1 > x2 ? 1 : 0);
+}
 
 template <int DIM>
 __device__ __forceinline__ df plane_df(const GridDF& gd, int a, int k) {
@@ -246,29 +273,9 @@ __device__ __forceinline__ df ev_df(const SegDF& s, const GridDF& gd, Ev e) {
   return r;
 }
 
-template <int DIM, class Ends>
-__device__ __forceinline__ void make_exact(const GridDev& g, SegDF& s, const Ends& ends) {
-  if (s.have_ex) return;
-  double P[3], Q[3];
-  ends(P, Q);
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) {
-    double D = Q[a] - P[a];
-    double inv = 1.0 / D;
-    s.ex_dl[a] = g.h[a] * inv;
-    s.ex_s0[a] = (g.o[a] - P[a]) * inv;
-  }
-  s.have_ex = true;
-}
-
-template <int DIM>
-__device__ __forceinline__ double ev_f64(const SegDF& s, Ev e) {
-  return e.ax < 0 ? (double)e.k : fma((double)e.k, pick<DIM>(s.ex_dl, e.ax), pick<DIM>(s.ex_s0, e.ax));
-}
-
 // exact sign of sigma(e1) - sigma(e2) given their double-float values
-template <int DIM, class Ends>
-__device__ __forceinline__ int cmp_vals(const GridDev& g, SegDF& s, Ev e1, df v1, Ev e2, df v2, const Ends& ends) {
+template <int DIM>
+__device__ __forceinline__ int cmp_vals(const GridDev& g, const SegDF& s, Ev e1, df v1, Ev e2, df v2, ExactRef ends) {
   if (e1.ax == e2.ax && e1.k == e2.k) return 0;
   if (e1.ax < 0 && e2.ax < 0) return e1.k < e2.k ? -1 : (e1.k > e2.k ? 1 : 0);
   float d = (v1.hi - v2.hi) + (v1.lo - v2.lo);
@@ -276,22 +283,19 @@ __device__ __forceinline__ int cmp_vals(const GridDev& g, SegDF& s, Ev e1, df v1
             (e2.ax < 0 ? 0.f : fmaf(pick<DIM>(s.E1, e2.ax), fabsf(v2.hi), pick<DIM>(s.E0, e2.ax)));
   if (d < -m) return -1;
   if (d > m) return 1;
-  make_exact<DIM>(g, s, ends);
-  double x1 = ev_f64<DIM>(s, e1), x2 = ev_f64<DIM>(s, e2);
-  return x1 < x2 ? -1 : (x1 > x2 ? 1 : 0);
+  return exact_cmp(ends, e1.ax, e1.k, e2.ax, e2.k);
 }
 
-template <int DIM, class Ends>
-__device__ __forceinline__ int cmp_ev(const GridDev& g, const GridDF& gd, SegDF& s, Ev e1, Ev e2, const Ends& ends) {
+template <int DIM>
+__device__ __forceinline__ int cmp_ev(const GridDev& g, const GridDF& gd, const SegDF& s, Ev e1, Ev e2, ExactRef ends) {
   return cmp_vals<DIM>(g, s, e1, ev_df<DIM>(s, gd, e1), e2, ev_df<DIM>(s, gd, e2), ends);
 }
 
 // Set-up.  Returns 0: the segment misses the grid; 1: ready for walk_df;
 // 2: the sign of some axis' extent cannot be certified (walk it in FP64).
-template <int DIM, class Ends>
+template <int DIM>
 __device__ __forceinline__ int seg_setup_df(const GridDev& g, const GridDF& gd, const df (&P)[3], const df (&Q)[3],
-                                            float mag, SegDF& s, const Ends& ends) {
-  s.have_ex = false;
+                                            float mag, SegDF& s, ExactRef ends) {
   float L2 = 0.f;
   // |V~ - V| <= eV for every vertex (double-float vertex formation, FP64 rounding)
   const float eV = 64.f * kEps44 * mag;
@@ -302,6 +306,7 @@ __device__ __forceinline__ int seg_setup_df(const GridDev& g, const GridDF& gd, 
     if (!(fabsf(Dh) > 4.f * eV + 4.f * kEps44 * fabsf(Dh))) return 2;
     L2 = fmaf(Dh, Dh, L2);
     s.P[a] = P[a];
+    s.D[a] = D;
     s.inv[a] = df_recip(D);
     s.dl[a] = df_mul(gd.h[a], s.inv[a]);
     s.step[a] = Dh > 0.f ? 1 : -1;
@@ -367,55 +372,241 @@ __device__ __forceinline__ int seg_setup_df(const GridDev& g, const GridDF& gd, 
   return 1;
 }
 
-// Walk a set-up segment, emitting (voxel, length) in path order.
-template <int DIM, bool kLengths, class Merge, class Sink, class Ends>
-__device__ __forceinline__ void walk_df(const GridDev& g, SegDF& s, Merge& mg, Sink& sink, const Ends& ends) {
-  Ev cur = s.in;
-  df vcur = s.s_in;
-  const int stride1 = g.n[0], stride2 = g.n[0] * g.n[1];
-  int col = s.idx[0] + stride1 * s.idx[1] + (DIM == 3 ? stride2 * s.idx[2] : 0);
-  int guard = g.n[0] + g.n[1] + (DIM == 3 ? g.n[2] : 0) + 2;
-  while (guard-- > 0) {
-    // axis (or axes, on an exact tie) whose next plane comes first
-    int m = 0;
-    unsigned mask = 1u;
-    df vm = s.sn[0];
+// FP32 walk state: crossing parameters as offsets from the segment's walk
+// origin (its grid entry s_in): ph_a = sigma of axis a's next plane - s_in,
+// computed as fmaf(kf_a, hv_a, ph0_a).  The common offset cancels in every
+// comparison; |ph~_a - ph_a| <= e0_a + 8u (|ph~_a| + ph0_a + hv_a).
+struct Walk32 {
+  float ph0[3], hv[3], e0[3], kf[3];
+  float send, esend;  // s_out - s_in and its bound
+};
+
+constexpr float kU32 = 5.9604645e-8f;  // 2^-24
+
+template <int DIM>
+__device__ __forceinline__ float w_err(const Walk32& w, int a, float ph) {
+  return fmaf(8.f * kU32, fabsf(ph) + pick<DIM>(w.ph0, a) + pick<DIM>(w.hv, a), pick<DIM>(w.e0, a));
+}
+
+// Interior fast path: both endpoints inside the grid by a margin, so
+// s_in = 0 and s_out = 1 exactly; the start voxel and the first phases come
+// from the double-float residual of P against its lower plane.  Returns
+// false when some residual is too close to a plane to certify (the caller
+// then uses seg_setup_df).
+template <int DIM>
+__device__ __forceinline__ bool seg_setup_fast(const GridDev& g, const GridDF& gd, const df (&P)[3], const df (&Q)[3],
+                                               float mag, SegDF& s, Walk32& w) {
+  const float eV = 64.f * kEps44 * mag;
+  float L2 = 0.f;
 #pragma unroll
-    for (int a = 1; a < DIM; ++a) {
-      int r = cmp_vals<DIM>(g, s, Ev{a, s.kn[a]}, s.sn[a], Ev{m, pick<DIM>(s.kn, m)}, vm, ends);
-      if (r < 0) {
-        m = a;
-        mask = 1u << a;
-        vm = s.sn[a];
-      } else if (r == 0) {
-        mask |= 1u << a;
-      }
-    }
-    const int km = pick<DIM>(s.kn, m);
-    bool final;
-    if (s.out.ax >= 0 && (mask >> s.out.ax & 1u) && pick<DIM>(s.kn, s.out.ax) == s.out.k)
-      final = true;  // the step crosses the exit plane itself
-    else
-      final = cmp_vals<DIM>(g, s, Ev{m, km}, vm, s.out, s.s_out, ends) >= 0;
-    float len = 0.f;
-    if (kLengths) {
-      df vend = final ? s.s_out : vm;
-      len = fmaxf(df_to_f(df_sub(vend, vcur)), 0.f) * s.L;
-    }
-    mg.emit(col, len, sink);
-    if (final) break;
-    cur = Ev{m, km};
-    vcur = vm;
+  for (int a = 0; a < DIM; ++a) {
+    const float lo = gd.of[a], span = (float)g.n[a] * gd.h[a].hi, m = 1e-3f * gd.h[a].hi;
+    if (!(P[a].hi > lo + m && P[a].hi < lo + span - m && Q[a].hi > lo + m && Q[a].hi < lo + span - m)) return false;
+  }
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      if (mask >> a & 1u) {
-        s.idx[a] += s.step[a];
-        s.kn[a] += s.step[a];
-        col += s.step[a] * (a == 0 ? 1 : (a == 1 ? stride1 : stride2));
-        s.sn[a] = df_add(s.sn[a], s.step[a] > 0 ? s.dl[a] : df_neg(s.dl[a]));
-      }
+  for (int a = 0; a < DIM; ++a) {
+    df D = df_sub(Q[a], P[a]);
+    float Dh = df_to_f(D);
+    if (!(fabsf(Dh) > 4.f * eV + 4.f * kEps44 * fabsf(Dh))) return false;
+    L2 = fmaf(Dh, Dh, L2);
+    const float h = gd.h[a].hi;
+    int i = (int)floorf((P[a].hi - gd.of[a]) * gd.rh[a]);
+    i = i < 0 ? 0 : (i > g.n[a] - 1 ? g.n[a] - 1 : i);
+    float r = df_to_f(df_sub(P[a], plane_df<DIM>(gd, a, i)));
+    if (r >= h) {
+      ++i;
+      r = df_to_f(df_sub(P[a], plane_df<DIM>(gd, a, i)));
+    } else if (r < 0.f) {
+      --i;
+      r = df_to_f(df_sub(P[a], plane_df<DIM>(gd, a, i)));
+    }
+    // |r~ - r| < eV + 2^-42 (|P| + |o| + n h); the FP64 definition decides a
+    // point on a plane differently from the reals only within 2^-50 of that
+    const float mr = 4.f * (eV + 16.f * kEps44 * (fabsf(P[a].hi) + fabsf(gd.of[a]) + (float)g.n[a] * h));
+    if (!(r > mr && r < h - mr) || i < 0 || i > g.n[a] - 1) return false;
+    const float aD = fabsf(Dh);
+    s.P[a] = P[a];
+    s.D[a] = D;
+    s.step[a] = Dh > 0.f ? 1 : -1;
+    s.idx[a] = i;
+    s.kn[a] = Dh > 0.f ? i + 1 : i;
+    w.ph0[a] = (Dh > 0.f ? (h - r) : r) / aD;
+    w.hv[a] = h / aD;
+    w.kf[a] = 0.f;
+    w.e0[a] = (2.f * mr) / aD + 4.f * kU32 * w.ph0[a];
+  }
+  s.L = sqrtf(L2);
+  s.in = Ev{-1, 0};
+  s.out = Ev{-1, 1};
+  s.s_in = df{0.f, 0.f};
+  s.s_out = df{1.f, 0.f};
+  w.send = 1.f;
+  w.esend = 0.f;
+  return true;
+}
+
+// convert a double-float set-up (seg_setup_df) into the FP32 walk state
+template <int DIM>
+__device__ __forceinline__ void walk_from_df(const SegDF& s, Walk32& w) {
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    float p0 = df_to_f(df_sub(s.sn[a], s.s_in));
+    w.ph0[a] = p0;
+    w.hv[a] = fabsf(s.dl[a].hi);
+    w.kf[a] = 0.f;
+    w.e0[a] = fmaf(s.E1[a], fabsf(s.sn[a].hi), s.E0[a]) + 4.f * kU32 * fabsf(p0);
+  }
+  w.send = df_to_f(df_sub(s.s_out, s.s_in));
+  w.esend = (s.out.ax < 0 ? 0.f : fmaf(pick<DIM>(s.E1, s.out.ax), fabsf(s.s_out.hi), pick<DIM>(s.E0, s.out.ax))) +
+            4.f * kU32 * fabsf(w.send);
+}
+
+// Lean FP32 walker of one set-up segment.  Per step: the smallest phase
+// certified against each other axis with one FFMA-formed bound, the exit
+// tested by plane index (exit through a grid plane) or against the segment
+// end, one fmaf to advance the stepped axis.  Anything the FP32 bounds cannot
+// decide (and every exact tie) goes to rare_decide().
+template <int DIM>
+struct Lean {
+  float ph[DIM], hv[DIM], ph0[DIM], kf[DIM];
+  float c[DIM];  // bound of ph~ at offset p: c + 8u p
+  float send, eend;
+  float pcur;
+  int kn[DIM], step[DIM], kexit[DIM], dcol[DIM];
+  int col, q, out_ax, out_k;
+  bool done;
+};
+
+template <int DIM>
+__device__ __forceinline__ void lean_begin(const GridDev& g, const SegDF& s, const Walk32& w, int q, Lean<DIM>& L) {
+  const int stride[3] = {1, g.n[0], g.n[0] * g.n[1]};
+  L.col = 0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    L.ph[a] = w.ph0[a];
+    L.ph0[a] = w.ph0[a];
+    L.hv[a] = w.hv[a];
+    L.kf[a] = 0.f;
+    L.c[a] = fmaf(8.f * kU32, w.ph0[a] + w.hv[a], w.e0[a]);
+    L.kn[a] = s.kn[a];
+    L.step[a] = s.step[a];
+    L.kexit[a] = (s.out.ax == a) ? s.out.k : -2147483647;
+    L.dcol[a] = s.step[a] * stride[a];
+    L.col += s.idx[a] * stride[a];
+  }
+  L.send = w.send;
+  L.eend = w.esend;
+  L.pcur = 0.f;
+  L.q = q;
+  L.out_ax = s.out.ax;
+  L.out_k = s.out.k;
+  L.done = false;
+}
+
+// Exact ordering of the axes' next planes (and against the segment end)
+// from double-float values rebuilt from the row record, then FP64 where the
+// double-float bounds cannot decide.
+template <int DIM>
+__device__ __forceinline__ void rare_decide(const RowDF& r, const BasisDF* tab, df Rdf, const GridDF& gd,
+                                            const GridDev& g, float mag, ExactRef ref, const Lean<DIM>& L,
+                                            unsigned& mask, int& m, bool& final) {
+  df P[3], Q[3];
+  vertex_df<DIM>(r, tab, Rdf, ref.q, P);
+  vertex_df<DIM>(r, tab, Rdf, ref.q + 1, Q);
+  const float eV = 64.f * kEps44 * mag;
+  int kn[3];
+  df v[4];
+  float e[4];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) kn[a] = L.kn[a];
+  // events 0..DIM-1: each axis' next plane; event DIM: the segment's end
+  for (int t = 0; t <= DIM; ++t) {
+    int a = (t < DIM) ? t : L.out_ax;
+    if (t == DIM && a < 0) {
+      v[t] = df{(float)L.out_k, 0.f};
+      e[t] = 0.f;
+      continue;
+    }
+    int k = (t < DIM) ? kn[a] : L.out_k;
+    df D = df_sub(Q[a], P[a]);
+    df inv = df_recip(D);
+    v[t] = df_mul(df_sub(df_add(gd.o[a], df_mul_f(gd.h[a], (float)k)), P[a]), inv);
+    float aD = fabsf(df_to_f(D));
+    float mx = (float)g.n[a] * fabsf(gd.h[a].hi) + fabsf(gd.o[a].hi) + fabsf(P[a].hi);
+    e[t] = 4.f * (16.f * kEps44 * mx + eV) / aD +
+           4.f * (16.f * kEps44 + (2.f * eV + 2.f * kEps44 * mag) / aD) * fabsf(v[t].hi);
+  }
+  auto cmp = [&](int t1, int t2) -> int {
+    float d = (v[t1].hi - v[t2].hi) + (v[t1].lo - v[t2].lo);
+    float mm = e[t1] + e[t2];
+    if (d < -mm) return -1;
+    if (d > mm) return 1;
+    int ax1 = t1 < DIM ? t1 : L.out_ax, k1 = t1 < DIM ? kn[t1] : L.out_k;
+    int ax2 = t2 < DIM ? t2 : L.out_ax, k2 = t2 < DIM ? kn[t2] : L.out_k;
+    if (ax1 == ax2 && k1 == k2) return 0;
+    return exact_cmp(ref, ax1, k1, ax2, k2);
+  };
+  m = 0;
+  for (int a = 1; a < DIM; ++a)
+    if (cmp(a, m) < 0) m = a;
+  mask = 1u << m;
+  for (int a = 0; a < DIM; ++a)
+    if (a != m && cmp(a, m) == 0) mask |= 1u << a;
+  if (L.out_ax >= 0 && (mask >> L.out_ax & 1u) && kn[L.out_ax] == L.out_k)
+    final = true;
+  else
+    final = cmp(m, DIM) >= 0;
+}
+
+template <int DIM>
+__device__ __forceinline__ float lean_step(Lean<DIM>& L, const RowDF& r, const BasisDF* tab, df Rdf,
+                                           const GridDF& gd, const GridDev& g, float mag, ExactRef ref) {
+  int m = 0;
+  float pm = L.ph[0];
+  bool unsure = false;
+#pragma unroll
+  for (int a = 1; a < DIM; ++a) {
+    const float e = fmaf(8.f * kU32, L.ph[a] + pm, L.c[a] + pick<DIM>(L.c, m));
+    if (L.ph[a] < pm - e) {
+      m = a;
+      pm = L.ph[a];
+    } else if (!(L.ph[a] > pm + e)) {
+      unsure = true;
     }
   }
+  unsigned mask = 1u << m;
+  bool final = false;
+  if (!unsure) {
+    if (pick<DIM>(L.kexit, m) == pick<DIM>(L.kn, m)) {
+      final = true;
+    } else {
+      const float e = fmaf(8.f * kU32, pm, pick<DIM>(L.c, m)) + L.eend;
+      if (pm > L.send + e)
+        final = true;
+      else if (!(pm < L.send - e))
+        unsure = true;
+    }
+  }
+  if (unsure) {
+    rare_decide<DIM>(r, tab, Rdf, gd, g, mag, ref, L, mask, m, final);
+    pm = pick<DIM>(L.ph, m);
+  }
+  const float len = fmaxf((final ? L.send : pm) - L.pcur, 0.f);
+  if (final) {
+    L.done = true;
+    return len;
+  }
+  L.pcur = pm;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    if (mask >> a & 1u) {
+      L.kf[a] += 1.f;
+      L.kn[a] += L.step[a];
+      L.col += L.dcol[a];
+      L.ph[a] = fmaf(L.kf[a], L.hv[a], L.ph0[a]);
+    }
+  }
+  return len;
 }
 
 }  // namespace pct
