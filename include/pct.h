@@ -203,6 +203,29 @@ pct_status pct_adjoint(const pct_phantom* ph, const pct_geometry* geo, const pct
                        int64_t row0, int64_t n_rows, const float* r_dev, float* g_dev,
                        void* workspace_dev, size_t workspace_bytes, void* stream);
 
+/* ---- allocation-free row pointers (no counterpart in the paper) ---------
+ * For callers that cannot allocate device memory: code inside a host
+ * application that owns every device allocation (a plugin with a fixed pool
+ * and no cudaMalloc of its own), or a latency-critical loop where cudaMalloc
+ * and cudaFree, which may synchronise the device, are not allowed.
+ * On entry row_ptr_dev[1..n_rows] hold int64 per-row entry counts (for
+ * example the differences of row pointers a caller already has, or counts it
+ * computed); on completion, in stream order, row_ptr_dev[0] = 0 and
+ * row_ptr_dev[i] = the sum of the first i counts -- the same result as the scan
+ * inside pct_simulate_count, without a workspace.  The scratch (one int64 per
+ * tile of rows) is a static device array sized for PCT_STATIC_SCAN_MAX_ROWS
+ * rows, 512 KB that every GPU loading this library holds until the process
+ * exits; larger n_rows return PCT_EINVAL with a message.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress, on the
+ * calling thread's current device); make that first call before any stream
+ * capture.  All calls share the one array: calls whose work overlaps on the
+ * GPU (other streams, other threads) race and corrupt each other's results --
+ * serialise them.  A call writes every scratch slot it reads, so nothing has to
+ * be cleared between calls.  No cudaMalloc, cudaFree or allocating library
+ * routine is called. */
+#define PCT_STATIC_SCAN_MAX_ROWS (1LL << 28)
+pct_status pct_scan_counts_static(int64_t* row_ptr_dev, int64_t n_rows, void* stream);
+
 /* message of the calling thread's last failure ("" if none) */
 const char* pct_last_error(void);
 

@@ -408,4 +408,9 @@ extern "C" pct_status pct_adjoint(const pct_phantom* ph, const pct_geometry* g, 
 
 extern "C" const char* pct_last_error(void) { return g_err.c_str(); }
 
+pct_status pct::set_error(pct_status st, const char* msg) {
+  g_err = msg;
+  return st;
+}
+
 extern "C" const char* pct_version(void) { return "libpct 0.1 (sm_103a)"; }

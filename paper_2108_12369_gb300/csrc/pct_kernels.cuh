@@ -4,6 +4,9 @@
 
 namespace pct {
 
+// records msg as the calling thread's pct_last_error() and returns st
+pct_status set_error(pct_status st, const char* msg);
+
 // rows scanned per block by the row-pointer scan
 constexpr int kScanTile = 4096;
 

@@ -61,7 +61,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 # every symbol include/pct.h declares
 EXPORTS = ["pct_phantom_create", "pct_phantom_destroy", "pct_phantom_nvox", "pct_phantom_rasterize",
            "pct_simulate_workspace_size", "pct_simulate_count", "pct_simulate_fill", "pct_simulate",
-           "pct_forward", "pct_adjoint", "pct_last_error", "pct_version"]
+           "pct_forward", "pct_adjoint", "pct_scan_counts_static", "pct_last_error", "pct_version"]
+STATIC_SCAN_MAX_ROWS = 1 << 28
 
 _lib = None
 
@@ -88,6 +89,7 @@ def lib():
                             C.c_int),
             "pct_adjoint": ([vp, P(Geometry), P(Csr), C.c_int64, C.c_int64, vp, vp, vp, C.c_size_t, vp],
                             C.c_int),
+            "pct_scan_counts_static": ([vp, C.c_int64, vp], C.c_int),
             "pct_last_error": ([], C.c_char_p),
             "pct_version": ([], C.c_char_p),
         }
@@ -244,6 +246,12 @@ def _csr(A):
     return C.byref(Csr(A["row_ptr"].numel() - 1, A["x_true"].numel() if "x_true" in A else 0,
                        A["col"].numel(), A["row_ptr"].data_ptr(), A["col"].data_ptr(),
                        A["val"].data_ptr(), 0, 0))
+
+
+def scan_counts_static(row_ptr, n_rows: int, stream=None):
+    """pct_scan_counts_static: row pointers from the counts in row_ptr[1..n_rows],
+    in place, with the library's static scratch (no device allocation)."""
+    _check(lib().pct_scan_counts_static(_ptr(row_ptr), int(n_rows), _stream(stream)))
 
 
 def forward(ph, geo, A, row0, n_rows, x, y, workspace=None, stream=None):
