@@ -203,6 +203,52 @@ pct_status pct_adjoint(const pct_phantom* ph, const pct_geometry* geo, const pct
                        int64_t row0, int64_t n_rows, const float* r_dev, float* g_dev,
                        void* workspace_dev, size_t workspace_bytes, void* stream);
 
+/* ---- batches: many simulations per launch -------------------------------
+ * Several independent simulations (different phantoms, grids, 2D / 3D, path
+ * models, sizes) share one persistent launch per phase: blocks take work
+ * items (simulation, block of 128 rows) from a device counter.  The count
+ * phase (raster, count, row pointers) and the fill phase are each captured
+ * once as a CUDA graph and replayed.  Mixed precision; the outputs of each
+ * simulation equal those of pct_simulate_count / pct_simulate_fill. */
+typedef struct {
+  const pct_phantom* phantom;  /* must outlive the batch */
+  pct_geometry geo;            /* its angles are read by pct_batch_create */
+  int64_t* row_ptr_dev;        /* [rows + 1], written by pct_batch_count */
+  float* x_true_dev;           /* [nvox], rasterised by pct_batch_count */
+} pct_batch_item;
+
+typedef struct pct_batch pct_batch; /* opaque */
+
+#define PCT_BATCH_AUTOTUNE 1 /* flags: time the launch shapes once and keep the fastest */
+
+/* bytes of device workspace pct_batch_create needs for these items */
+pct_status pct_batch_workspace_size(const pct_batch_item* items, int32_t n, size_t* bytes);
+
+/* Uploads every simulation's tables into the workspace, orders the work
+ * items, optionally autotunes the launch shape (runs the count phase a few
+ * times and synchronises; the choice is cached per batch signature in the
+ * process) and captures the graphs.  The workspace and the item buffers must
+ * stay valid until pct_batch_destroy. */
+pct_status pct_batch_create(const pct_batch_item* items, int32_t n, void* workspace_dev, size_t workspace_bytes,
+                            int32_t flags, void* stream, pct_batch** out);
+
+/* count phase for all items (graph launch on stream) */
+pct_status pct_batch_count(pct_batch* batch, void* stream);
+
+/* nnz of every item after pct_batch_count: host array [n]; synchronises stream */
+pct_status pct_batch_nnz(pct_batch* batch, int64_t* nnz, void* stream);
+
+/* fill phase: col_dev[k], val_dev[k], b_dev[k] are item k's outputs (host
+ * arrays of n device pointers) */
+pct_status pct_batch_fill(pct_batch* batch, int32_t* const* col_dev, float* const* val_dev, float* const* b_dev,
+                          void* stream);
+
+/* the launch shape in use: grid multiplier (x resident blocks per SM) and item
+ * order (0: item order, 1: largest simulation first) */
+pct_status pct_batch_params(const pct_batch* batch, int32_t* grid_mult, int32_t* order);
+
+pct_status pct_batch_destroy(pct_batch* batch);
+
 /* ---- allocation-free row pointers (no counterpart in the paper) ---------
  * For callers that cannot allocate device memory: code inside a host
  * application that owns every device allocation (a plugin with a fixed pool

@@ -10,7 +10,12 @@
 #include <string>
 #include <vector>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
+
 #include "pct_kernels.cuh"
+#include "pct_mixed.cuh"
 
 using namespace pct;
 
@@ -404,6 +409,310 @@ extern "C" pct_status pct_adjoint(const pct_phantom* ph, const pct_geometry* g, 
   if (row0 + n_rows > L.rows) return fail(PCT_EINVAL, "row range beyond the geometry");
   launch_mf_adjoint_f64(S, row0, n_rows, r, gout, st);
   return cuda_check("matrix-free adjoint");
+}
+
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+struct pct_batch {
+  int n = 0;
+  std::vector<pct_batch_item> items;      // as given
+  std::vector<Layout> layouts;
+  std::vector<size_t> base;               // workspace offset of each item's region
+  std::vector<SimDev> sims;
+  std::vector<BatchInst> inst;            // processing order
+  std::vector<int> order;                 // processing position -> item index
+  BatchInst* d_inst = nullptr;
+  unsigned long long* d_next = nullptr;   // two counters (2D, 3D launches)
+  long long first3 = 0, total = 0;
+  int grid_mult = 1, order_mode = 0;
+  int bps[2][2] = {{1, 1}, {1, 1}};       // resident blocks per SM [fill][dim 3]
+  int sms = 1;
+  cudaGraphExec_t e_count = nullptr, e_fill = nullptr;
+  cudaGraph_t g_count = nullptr, g_fill = nullptr;
+};
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<unsigned long long, std::pair<int, int>> g_tune_cache;  // signature -> (grid mult, order)
+
+unsigned long long batch_signature(const pct_batch& b) {
+  unsigned long long h = 1469598103934665603ULL;
+  auto mix = [&](unsigned long long v) {
+    h ^= v;
+    h *= 1099511628211ULL;
+  };
+  for (int k = 0; k < b.n; ++k) {
+    const pct_batch_item& it = b.items[k];
+    mix((unsigned long long)it.phantom->dev.g.dim);
+    for (int a = 0; a < 3; ++a) mix((unsigned long long)it.phantom->dev.g.n[a]);
+    mix((unsigned long long)b.layouts[k].rows);
+    mix((unsigned long long)it.geo.model.model);
+  }
+  return h;
+}
+
+void batch_phase(pct_batch& b, bool fill, cudaStream_t st) {
+  if (!fill) {
+    for (int k = 0; k < b.n; ++k)
+      launch_raster(b.items[k].phantom->dev, b.items[k].x_true_dev, b.items[k].phantom->nvox, st);
+  }
+  const int f = fill ? 1 : 0;
+  launch_batch(fill, 2, b.d_inst, b.n, 0, b.first3, b.d_next, b.sms * b.bps[f][0] * b.grid_mult, st);
+  launch_batch(fill, 3, b.d_inst, b.n, b.first3, b.total, b.d_next + 1, b.sms * b.bps[f][1] * b.grid_mult, st);
+  if (!fill) {
+    for (int k = 0; k < b.n; ++k)
+      launch_scan_rowptr((long long*)b.items[k].row_ptr_dev, b.layouts[k].rows,
+                         (long long*)((char*)b.sims[k].cs - b.layouts[k].cs + b.layouts[k].partial), st);
+  }
+}
+
+pct_status batch_capture(pct_batch& b, bool fill) {
+  cudaStream_t cap;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return cuda_check("capture stream");
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t e = nullptr;
+  bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    batch_phase(b, fill, cap);
+    ok = cudaStreamEndCapture(cap, &g) == cudaSuccess;
+  }
+  if (ok) ok = cudaGraphInstantiate(&e, g, 0) == cudaSuccess;
+  cudaStreamDestroy(cap);
+  if (!ok) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_check("graph capture");
+  }
+  if (fill) {
+    b.g_fill = g;
+    b.e_fill = e;
+  } else {
+    b.g_count = g;
+    b.e_count = e;
+  }
+  return PCT_OK;
+}
+
+}  // namespace
+
+extern "C" pct_status pct_batch_workspace_size(const pct_batch_item* items, int32_t n, size_t* bytes) {
+  if (!items || n < 1 || !bytes) return fail(PCT_EINVAL, "pct_batch_workspace_size: bad arguments");
+  size_t off = 0;
+  for (int k = 0; k < n; ++k) {
+    pct_status rc = check_geometry(items[k].phantom, &items[k].geo, PCT_PREC_MIXED);
+    if (rc != PCT_OK) return rc;
+    off = align256(off + layout_of(items[k].phantom, &items[k].geo, PCT_PREC_MIXED).total);
+  }
+  off = align256(off + sizeof(BatchInst) * (size_t)n);
+  off = align256(off + 2 * sizeof(unsigned long long));
+  *bytes = off;
+  return PCT_OK;
+}
+
+extern "C" pct_status pct_batch_destroy(pct_batch* b) {
+  if (!b) return PCT_OK;
+  if (b->e_count) cudaGraphExecDestroy(b->e_count);
+  if (b->e_fill) cudaGraphExecDestroy(b->e_fill);
+  if (b->g_count) cudaGraphDestroy(b->g_count);
+  if (b->g_fill) cudaGraphDestroy(b->g_fill);
+  delete b;
+  return PCT_OK;
+}
+
+extern "C" pct_status pct_batch_create(const pct_batch_item* items, int32_t n, void* ws, size_t ws_bytes,
+                                       int32_t flags, void* stream, pct_batch** out) {
+  if (!out) return fail(PCT_EINVAL, "pct_batch_create: out is NULL");
+  *out = nullptr;
+  size_t need = 0;
+  pct_status rc = pct_batch_workspace_size(items, n, &need);
+  if (rc != PCT_OK) return rc;
+  if (!ws || ws_bytes < need) return fail(PCT_ENOMEM, "batch workspace of %zu bytes is smaller than %zu", ws_bytes, need);
+  cudaStream_t st = (cudaStream_t)stream;
+  pct_batch* b = new (std::nothrow) pct_batch;
+  if (!b) return fail(PCT_ENOMEM, "out of host memory");
+  b->n = n;
+  b->items.assign(items, items + n);
+  b->layouts.resize(n);
+  b->base.resize(n);
+  b->sims.resize(n);
+  char* base = (char*)ws;
+  size_t off = 0;
+  for (int k = 0; k < n; ++k) {
+    const pct_batch_item& it = items[k];
+    Layout L = layout_of(it.phantom, &it.geo, PCT_PREC_MIXED);
+    if (L.rows > 0 && (!it.row_ptr_dev || !it.x_true_dev)) {
+      pct_batch_destroy(b);
+      return fail(PCT_EINVAL, "batch item %d: NULL row_ptr_dev or x_true_dev", k);
+    }
+    b->base[k] = off;
+    Layout L2;
+    rc = make_sim(it.phantom, &it.geo, PCT_PREC_MIXED, base + off, L.total, st, b->sims[k], L2);
+    if (rc != PCT_OK) {
+      pct_batch_destroy(b);
+      return rc;
+    }
+    b->layouts[k] = L2;
+    off = align256(off + L.total);
+  }
+  b->d_inst = (BatchInst*)(base + off);
+  off = align256(off + sizeof(BatchInst) * (size_t)n);
+  b->d_next = (unsigned long long*)(base + off);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  for (int f = 0; f < 2; ++f)
+    for (int d = 0; d < 2; ++d) b->bps[f][d] = batch_blocks_per_sm(f == 1, d == 0 ? 2 : 3);
+  // instance table contents (order-independent fields)
+  std::vector<BatchInst> by_item(n);
+  for (int k = 0; k < n; ++k) {
+    BatchInst& I = by_item[k];
+    memset(&I, 0, sizeof(I));
+    I.S = b->sims[k];
+    I.M = mix_args(b->sims[k], b->layouts[k].rows, (const char*)b->sims[k].cs - b->layouts[k].cs + b->layouts[k].basis32,
+                   (char*)b->sims[k].cs - b->layouts[k].cs + b->layouts[k].rec);
+    I.n = b->layouts[k].rows;
+    I.row_ptr_w = (long long*)items[k].row_ptr_dev;
+    I.row_ptr = (const long long*)items[k].row_ptr_dev;
+    I.x = items[k].x_true_dev;
+  }
+  auto arrange = [&]() -> pct_status {
+    std::vector<BatchInst> saved = by_item;
+    pct_status r = PCT_OK;
+    // batch_arrange fills item0 in processing order; copy the item fields first
+    b->order.resize(n);
+    for (int k = 0; k < n; ++k) b->order[k] = k;
+    b->inst = saved;
+    std::vector<int> ord(n);
+    for (int k = 0; k < n; ++k) ord[k] = k;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+      int dx = items[x].phantom->dev.g.dim, dy = items[y].phantom->dev.g.dim;
+      if (dx != dy) return dx < dy;
+      if (b->order_mode == 1) return b->layouts[x].rows > b->layouts[y].rows;
+      return false;
+    });
+    for (int pos = 0; pos < n; ++pos) b->inst[pos] = saved[ord[pos]];
+    b->order = ord;
+    long long item = 0;
+    b->first3 = -1;
+    for (int pos = 0; pos < n; ++pos) {
+      if (b->first3 < 0 && b->inst[pos].S.ph.g.dim == 3) b->first3 = item;
+      b->inst[pos].item0 = item;
+      item += (b->inst[pos].n + 127) / 128;
+    }
+    b->total = item;
+    if (b->first3 < 0) b->first3 = item;
+    if (cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      r = cuda_check("batch table upload");
+    if (cudaStreamSynchronize(st) != cudaSuccess) r = cuda_check("batch table upload");
+    return r;
+  };
+  const unsigned long long sig = batch_signature(*b);
+  bool cached = false;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto itc = g_tune_cache.find(sig);
+    if (itc != g_tune_cache.end()) {
+      b->grid_mult = itc->second.first;
+      b->order_mode = itc->second.second;
+      cached = true;
+    }
+  }
+  if ((flags & PCT_BATCH_AUTOTUNE) && !cached) {
+    // time the count phase for each launch shape; keep the fastest
+    const int mults[2] = {1, 2};
+    float best = 1e30f;
+    int bm = 1, bo = 0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int om = 0; om < 2; ++om) {
+      for (int mi = 0; mi < 2; ++mi) {
+        b->order_mode = om;
+        b->grid_mult = mults[mi];
+        if ((rc = arrange()) != PCT_OK) break;
+        batch_phase(*b, false, st);  // warm-up
+        cudaEventRecord(e0, st);
+        batch_phase(*b, false, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          rc = cuda_check("autotune");
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          bm = mults[mi];
+          bo = om;
+        }
+      }
+      if (rc != PCT_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != PCT_OK) {
+      pct_batch_destroy(b);
+      return rc;
+    }
+    b->grid_mult = bm;
+    b->order_mode = bo;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[sig] = std::make_pair(bm, bo);
+  }
+  if ((rc = arrange()) != PCT_OK || (rc = batch_capture(*b, false)) != PCT_OK ||
+      (rc = batch_capture(*b, true)) != PCT_OK) {
+    pct_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return PCT_OK;
+}
+
+extern "C" pct_status pct_batch_count(pct_batch* b, void* stream) {
+  if (!b || !b->e_count) return fail(PCT_EINVAL, "pct_batch_count: no batch");
+  if (cudaGraphLaunch(b->e_count, (cudaStream_t)stream) != cudaSuccess) return cuda_check("batch count graph");
+  return PCT_OK;
+}
+
+extern "C" pct_status pct_batch_nnz(pct_batch* b, int64_t* nnz, void* stream) {
+  if (!b || !nnz) return fail(PCT_EINVAL, "pct_batch_nnz: NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int k = 0; k < b->n; ++k) {
+    nnz[k] = 0;
+    if (b->layouts[k].rows > 0 &&
+        cudaMemcpyAsync(&nnz[k], b->items[k].row_ptr_dev + b->layouts[k].rows, sizeof(int64_t),
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      return cuda_check("batch nnz");
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check("batch nnz");
+  return PCT_OK;
+}
+
+extern "C" pct_status pct_batch_fill(pct_batch* b, int32_t* const* col, float* const* val, float* const* bout,
+                                     void* stream) {
+  if (!b || !b->e_fill || !col || !val || !bout) return fail(PCT_EINVAL, "pct_batch_fill: NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int pos = 0; pos < b->n; ++pos) {
+    int k = b->order[pos];
+    if (b->layouts[k].rows > 0 && !bout[k]) return fail(PCT_EINVAL, "batch item %d: NULL b", k);
+    b->inst[pos].col = (int*)col[k];
+    b->inst[pos].val = val[k];
+    b->inst[pos].b = bout[k];
+  }
+  // the graph reads the output pointers from the instance table in global
+  // memory, so updating the table is enough (the copy is staged before return)
+  if (cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(BatchInst) * b->n, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return cuda_check("batch table upload");
+  if (cudaGraphLaunch(b->e_fill, st) != cudaSuccess) return cuda_check("batch fill graph");
+  return PCT_OK;
+}
+
+extern "C" pct_status pct_batch_params(const pct_batch* b, int32_t* grid_mult, int32_t* order) {
+  if (!b || !grid_mult || !order) return fail(PCT_EINVAL, "pct_batch_params: NULL argument");
+  *grid_mult = b->grid_mult;
+  *order = b->order_mode;
+  return PCT_OK;
 }
 
 extern "C" const char* pct_last_error(void) { return g_err.c_str(); }

@@ -9,13 +9,6 @@
 
 namespace pct {
 
-struct MixArgs {
-  GridDF gd;
-  df R;                 // lead length, double-float
-  const BasisDF* tab;   // [K + 1]
-  RowDF* rdf;           // [rows]
-  PathF64* r64;         // [rows]
-};
 
 // feeds FP64-walked entries into the FP32 row merge
 template <class M>
@@ -193,10 +186,13 @@ __device__ __forceinline__ long long regroup_rows(long long row, int key) {
 
 __device__ __forceinline__ int nv_key(int nv) { return nv <= 2 ? 0 : (nv <= 4 ? 1 : 2); }
 
+// One block of 128 consecutive rows starting at row0 (count phase).  The
+// arguments may live in parameter space (one launch per simulation) or in
+// global memory (the batch kernel).
 template <int DIM>
-__global__ void __launch_bounds__(128) k_count_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
-                                                     long long n, long long* __restrict__ counts) {
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void count_block(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
+                                            long long n, long long row0, long long* __restrict__ counts) {
+  long long i = row0 + threadIdx.x;
   int key = -1;
   if (i < n) {
     PathF64 p = path_setup(S, i);
@@ -216,12 +212,18 @@ __global__ void __launch_bounds__(128) k_count_mixed(SimDev S, MixArgs M, const 
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(128) k_fill_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
-                                                    long long n,
-                                                    const long long* __restrict__ row_ptr,
-                                                    const float* __restrict__ x, int* __restrict__ col,
-                                                    float* __restrict__ val, float* __restrict__ b) {
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(128) k_count_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
+                                                     long long n, long long* __restrict__ counts) {
+  count_block<DIM>(S, M, Sg, gdg, n, (long long)blockIdx.x * blockDim.x, counts);
+}
+
+// One block of 128 consecutive rows starting at row0 (fill phase).
+template <int DIM>
+__device__ __forceinline__ void fill_block(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
+                                           long long n, long long row0, const long long* __restrict__ row_ptr,
+                                           const float* __restrict__ x, int* __restrict__ col,
+                                           float* __restrict__ val, float* __restrict__ b) {
+  long long i = row0 + threadIdx.x;
   int key = (i < n) ? nv_key(M.rdf[i].nv) : -1;
   long long row = regroup_rows(i, key);
   const bool live = row >= 0;
@@ -247,12 +249,75 @@ __global__ void __launch_bounds__(128) k_fill_mixed(SimDev S, MixArgs M, const S
   if (live) b[row] = fs.sum * r.fac;
 }
 
+template <int DIM>
+__global__ void __launch_bounds__(128) k_fill_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
+                                                    long long n, const long long* __restrict__ row_ptr,
+                                                    const float* __restrict__ x, int* __restrict__ col,
+                                                    float* __restrict__ val, float* __restrict__ b) {
+  fill_block<DIM>(S, M, Sg, gdg, n, (long long)blockIdx.x * blockDim.x, row_ptr, x, col, val, b);
+}
+
+// ---------------------------------------------------------------------------
+// Batch: one persistent launch over the work items (instance, block of 128
+// rows) of many heterogeneous simulations.  A block takes the next item from
+// a device counter; items are independent, so nothing ever waits.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int batch_find(const BatchInst* __restrict__ B, int n_inst, long long item) {
+  int lo = 0, hi = n_inst - 1;  // last instance whose first item is <= item
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (B[mid].item0 <= item)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <bool kFill, int DIM>
+__global__ void __launch_bounds__(128) k_batch(const BatchInst* __restrict__ B, int n_inst, long long first,
+                                               long long last, unsigned long long* next) {
+  __shared__ long long item_s;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) item_s = first + (long long)atomicAdd(next, 1ULL);
+    __syncthreads();
+    const long long item = item_s;
+    if (item >= last) return;
+    const BatchInst& I = B[batch_find(B, n_inst, item)];
+    const long long row0 = (item - I.item0) * 128;
+    if (kFill)
+      fill_block<DIM>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, I.row_ptr, I.x, I.col, I.val, I.b);
+    else
+      count_block<DIM>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, I.row_ptr_w + 1);
+  }
+}
+
+int batch_blocks_per_sm(bool fill, int dim) {
+  int nb = 0;
+  if (fill && dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<true, 2>, 128, 0);
+  if (fill && dim == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<true, 3>, 128, 0);
+  if (!fill && dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<false, 2>, 128, 0);
+  if (!fill && dim == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<false, 3>, 128, 0);
+  return nb > 0 ? nb : 1;
+}
+
+void launch_batch(bool fill, int dim, const BatchInst* B, int n_inst, long long first, long long last,
+                  unsigned long long* next, int grid, cudaStream_t st) {
+  cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
+  if (last <= first || n_inst <= 0) return;
+  if (fill && dim == 2) k_batch<true, 2><<<grid, 128, 0, st>>>(B, n_inst, first, last, next);
+  if (fill && dim == 3) k_batch<true, 3><<<grid, 128, 0, st>>>(B, n_inst, first, last, next);
+  if (!fill && dim == 2) k_batch<false, 2><<<grid, 128, 0, st>>>(B, n_inst, first, last, next);
+  if (!fill && dim == 3) k_batch<false, 3><<<grid, 128, 0, st>>>(B, n_inst, first, last, next);
+}
+
 static df split_host(double v) {
   float hi = (float)v;
   return df{hi, (float)(v - (double)hi)};
 }
 
-static MixArgs mix_args(const SimDev& S, long long n, const void* tab, void* rec) {
+MixArgs mix_args(const SimDev& S, long long n, const void* tab, void* rec) {
   MixArgs M;
   for (int a = 0; a < 3; ++a) {
     M.gd.o[a] = split_host(S.ph.g.o[a]);

@@ -242,7 +242,7 @@ __device__ __forceinline__ double sigma_f64(const GridDev& g, const double P[3],
 
 // exact sign of sigma(e1) - sigma(e2) from the FP64 definition (rare: only
 // where the double-float bounds cannot decide, in practice exact ties)
-__device__ __noinline__ int exact_cmp(ExactRef ref, int ax1, int k1, int ax2, int k2) {
+static __device__ __noinline__ int exact_cmp(ExactRef ref, int ax1, int k1, int ax2, int k2) {
   const SimDev& S = *ref.S;
   double P[3], Q[3];
   path_vertex(S, *ref.p, ref.q, P);
@@ -608,5 +608,35 @@ __device__ __forceinline__ float lean_step(Lean<DIM>& L, const RowDF& r, const B
   }
   return len;
 }
+
+// kernel arguments of the mixed form besides SimDev
+struct MixArgs {
+  GridDF gd;
+  df R;                 // lead length, double-float
+  const BasisDF* tab;   // [K + 1]
+  RowDF* rdf;           // [rows]
+  PathF64* r64;         // [rows]
+};
+
+// one simulation of a batch (a global-memory copy of its arguments and its
+// outputs); item0 = its first work item (block of 128 rows)
+struct BatchInst {
+  SimDev S;
+  MixArgs M;
+  long long n;
+  long long item0;
+  long long* row_ptr_w;     // [n + 1]: counts go to row_ptr_w[1..n]
+  const long long* row_ptr; // the same array, read by the fill
+  const float* x;
+  int* col;
+  float* val;
+  float* b;
+};
+
+MixArgs mix_args(const SimDev& S, long long n, const void* tab, void* rec);
+// persistent launch over the items [first, last) (all of dimension dim)
+int batch_blocks_per_sm(bool fill, int dim);
+void launch_batch(bool fill, int dim, const BatchInst* B, int n_inst, long long first, long long last,
+                  unsigned long long* next, int grid, cudaStream_t st);
 
 }  // namespace pct

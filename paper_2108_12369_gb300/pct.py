@@ -55,13 +55,21 @@ class Csr(C.Structure):
                 ("b", C.c_void_p), ("x_true", C.c_void_p)]
 
 
+class BatchItem(C.Structure):
+    _fields_ = [("phantom", C.c_void_p), ("geo", Geometry), ("row_ptr_dev", C.c_void_p),
+                ("x_true_dev", C.c_void_p)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 # every symbol include/pct.h declares
 EXPORTS = ["pct_phantom_create", "pct_phantom_destroy", "pct_phantom_nvox", "pct_phantom_rasterize",
            "pct_simulate_workspace_size", "pct_simulate_count", "pct_simulate_fill", "pct_simulate",
-           "pct_forward", "pct_adjoint", "pct_scan_counts_static", "pct_last_error", "pct_version"]
+           "pct_forward", "pct_adjoint", "pct_batch_workspace_size", "pct_batch_create",
+           "pct_batch_count", "pct_batch_nnz", "pct_batch_fill", "pct_batch_params", "pct_batch_destroy",
+           "pct_scan_counts_static", "pct_last_error", "pct_version"]
+BATCH_AUTOTUNE = 1
 STATIC_SCAN_MAX_ROWS = 1 << 28
 
 _lib = None
@@ -90,6 +98,13 @@ def lib():
             "pct_adjoint": ([vp, P(Geometry), P(Csr), C.c_int64, C.c_int64, vp, vp, vp, C.c_size_t, vp],
                             C.c_int),
             "pct_scan_counts_static": ([vp, C.c_int64, vp], C.c_int),
+            "pct_batch_workspace_size": ([P(BatchItem), C.c_int32, P(C.c_size_t)], C.c_int),
+            "pct_batch_create": ([P(BatchItem), C.c_int32, vp, C.c_size_t, C.c_int32, vp, P(vp)], C.c_int),
+            "pct_batch_count": ([vp, vp], C.c_int),
+            "pct_batch_nnz": ([vp, P(C.c_int64), vp], C.c_int),
+            "pct_batch_fill": ([vp, P(vp), P(vp), P(vp), vp], C.c_int),
+            "pct_batch_params": ([vp, P(C.c_int32), P(C.c_int32)], C.c_int),
+            "pct_batch_destroy": ([vp], C.c_int),
             "pct_last_error": ([], C.c_char_p),
             "pct_version": ([], C.c_char_p),
         }
@@ -268,3 +283,69 @@ def adjoint(ph, geo, A, row0, n_rows, r, g, workspace=None, stream=None):
     _check(lib().pct_adjoint(ph.handle if ph else None, C.byref(geo.c) if geo else None, _csr(A),
                              row0, n_rows, _ptr(r), _ptr(g), _ptr(ws),
                              0 if ws is None else ws.numel() * ws.element_size(), _stream(stream)))
+
+
+class Batch:
+    """pct_batch_* over a list of workload dicts: one persistent launch per
+    phase for all of them, replayed from CUDA graphs."""
+
+    def __init__(self, workloads, autotune: bool = False, stream=None, device="cuda"):
+        import torch
+        self.n = len(workloads)
+        self.phantoms = [Phantom(w["phantom"]) for w in workloads]
+        self.geos = [GeometryArgs(w) for w in workloads]
+        self.row_ptr = [torch.empty(g.n_rows + 1, dtype=torch.int64, device=device) for g in self.geos]
+        self.x_true = [torch.empty(max(p.nvox, 1), dtype=torch.float32, device=device) for p in self.phantoms]
+        self._items = (BatchItem * self.n)(*[
+            BatchItem(p.handle, g.c, rp.data_ptr(), x.data_ptr())
+            for p, g, rp, x in zip(self.phantoms, self.geos, self.row_ptr, self.x_true)])
+        nbytes = C.c_size_t()
+        _check(lib().pct_batch_workspace_size(self._items, self.n, C.byref(nbytes)))
+        self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=device)
+        self.handle = C.c_void_p()
+        _check(lib().pct_batch_create(self._items, self.n, _ptr(self.workspace), nbytes.value,
+                                      BATCH_AUTOTUNE if autotune else 0, _stream(stream),
+                                      C.byref(self.handle)))
+        self.device = device
+
+    def count(self, stream=None):
+        _check(lib().pct_batch_count(self.handle, _stream(stream)))
+
+    def nnz(self, stream=None):
+        out = (C.c_int64 * self.n)()
+        _check(lib().pct_batch_nnz(self.handle, out, _stream(stream)))
+        return [int(v) for v in out]
+
+    def fill(self, nnz=None, stream=None):
+        """Allocates col / val / b per simulation and runs the fill phase."""
+        import torch
+        nnz = self.nnz(stream) if nnz is None else nnz
+        self.col = [torch.empty(max(z, 1), dtype=torch.int32, device=self.device) for z in nnz]
+        self.val = [torch.empty(max(z, 1), dtype=torch.float32, device=self.device) for z in nnz]
+        self.b = [torch.empty(max(g.n_rows, 1), dtype=torch.float32, device=self.device) for g in self.geos]
+        cols = (C.c_void_p * self.n)(*[t.data_ptr() for t in self.col])
+        vals = (C.c_void_p * self.n)(*[t.data_ptr() for t in self.val])
+        bs = (C.c_void_p * self.n)(*[t.data_ptr() for t in self.b])
+        _check(lib().pct_batch_fill(self.handle, cols, vals, bs, _stream(stream)))
+        return [{"row_ptr": rp, "col": c[:z], "val": v[:z], "b": bb[:g.n_rows], "x_true": x, "nnz": z}
+                for rp, c, v, bb, x, z, g in zip(self.row_ptr, self.col, self.val, self.b, self.x_true,
+                                                  nnz, self.geos)]
+
+    def params(self):
+        gm, order = C.c_int32(), C.c_int32()
+        _check(lib().pct_batch_params(self.handle, C.byref(gm), C.byref(order)))
+        return gm.value, order.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.pct_batch_destroy(self.handle)
+            self.handle = None
+
+
+def batch_workspace_size(workloads) -> int:
+    phs = [Phantom(w["phantom"]) for w in workloads]
+    geos = [GeometryArgs(w) for w in workloads]
+    items = (BatchItem * len(phs))(*[BatchItem(p.handle, g.c, None, None) for p, g in zip(phs, geos)])
+    n = C.c_size_t()
+    _check(lib().pct_batch_workspace_size(items, len(phs), C.byref(n)))
+    return n.value

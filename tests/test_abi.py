@@ -80,3 +80,12 @@ def test_workspace_size_and_geometry_checks(pct):
         pct.simulate_workspace_size(ph, geo, 7)
     w0 = dict(w, angles=W.angles(0))
     assert pct.simulate_workspace_size(ph, pct.GeometryArgs(w0), pct.PREC_F64) > 0
+
+
+def test_batch_workspace_size_validates(pct):
+    ws = [W.neo1_2d_straight(n_angles=3, paths_per_angle=10), W.head_3d_spline(n_angles=2, paths_per_angle=5)]
+    assert pct.batch_workspace_size(ws) > 0
+    bad = [dict(ws[0], model=dict(ws[0]["model"], model=9))]
+    with pytest.raises(pct.PctError) as e:
+        pct.batch_workspace_size(bad)
+    assert e.value.status == pct.EINVAL
