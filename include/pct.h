@@ -188,18 +188,27 @@ pct_status pct_simulate(const pct_phantom* ph, const pct_geometry* geo, int32_t 
 
 /* ---- projectors: y = A x and g += A^T r (Sec. II, A x = b) -------------- */
 
-/* y_dev[i] = sum_j A_ij x_dev[j] for rows [row0, row0 + n_rows).  With
- * A != NULL the CSR is used (row indices are global; y_dev has n_rows
- * entries); with A == NULL the rows are regenerated from the geometry
- * (matrix-free, paths recomputed) with exact chord lengths. */
-pct_status pct_forward(const pct_phantom* ph, const pct_geometry* geo, const pct_csr* A,
+/* Workspace for the matrix-free projectors on chunks of at most max_rows
+ * rows (angle / basis tables and per-row records of one chunk). */
+pct_status pct_projector_workspace_size(const pct_phantom* ph, const pct_geometry* geo, int32_t precision,
+                                        int64_t max_rows, size_t* bytes);
+
+/* y_dev[i - row0] = sum_j A_ij x_dev[j] for rows [row0, row0 + n_rows).
+ * With A != NULL the CSR is used (HBM-bound, 8 bytes per nonzero; geo,
+ * precision and the workspace are ignored).  With A == NULL the rows are
+ * regenerated from the geometry (matrix-free: the same paths, voxels and
+ * lengths as pct_simulate_fill, nothing stored) in the given precision, with
+ * a workspace of pct_projector_workspace_size(..., n_rows) bytes; this is how
+ * systems too large for HBM are projected, chunk by chunk. */
+pct_status pct_forward(const pct_phantom* ph, const pct_geometry* geo, const pct_csr* A, int32_t precision,
                        int64_t row0, int64_t n_rows, const float* x_dev, float* y_dev,
                        void* workspace_dev, size_t workspace_bytes, void* stream);
 
 /* g_dev[j] += sum_i A_ij r_dev[i - row0] over rows [row0, row0 + n_rows)
  * (accumulates, so chunks can be summed; the caller zeroes g_dev first).
- * FP32 atomic accumulation: the order of additions is not fixed. */
-pct_status pct_adjoint(const pct_phantom* ph, const pct_geometry* geo, const pct_csr* A,
+ * FP32 atomic accumulation: the order of additions is not fixed.  Rows with
+ * r_i = 0 are skipped.  Arguments as for pct_forward. */
+pct_status pct_adjoint(const pct_phantom* ph, const pct_geometry* geo, const pct_csr* A, int32_t precision,
                        int64_t row0, int64_t n_rows, const float* r_dev, float* g_dev,
                        void* workspace_dev, size_t workspace_bytes, void* stream);
 

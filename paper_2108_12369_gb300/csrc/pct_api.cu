@@ -167,7 +167,8 @@ pct_status check_geometry(const pct_phantom* ph, const pct_geometry* g, int prec
   return PCT_OK;
 }
 
-Layout layout_of(const pct_phantom*, const pct_geometry* g, int precision) {
+// rec_rows >= 0 sizes the row records for that many rows (projector chunks)
+Layout layout_of(const pct_phantom*, const pct_geometry* g, int precision, long long rec_rows = -1) {
   Layout L;
   L.rows = (long long)g->n_angles * g->paths_per_angle;
   L.K = (g->model.model == PCT_PATH_SPLINE) ? g->model.spline_segments : 1;
@@ -183,17 +184,17 @@ Layout layout_of(const pct_phantom*, const pct_geometry* g, int precision) {
   L.args = off;
   off = align256(off + mixed_args_bytes());
   L.rec = off;
-  if (precision == PCT_PREC_MIXED) off = align256(off + mixed_record_size(L.rows));
+  if (precision == PCT_PREC_MIXED) off = align256(off + mixed_record_size(rec_rows >= 0 ? rec_rows : L.rows));
   L.total = off;
   return L;
 }
 
 // the simulation's kernel arguments; uploads the angle and basis tables
 pct_status make_sim(const pct_phantom* ph, const pct_geometry* g, int precision, void* ws, size_t ws_bytes,
-                    cudaStream_t st, SimDev& S, Layout& L) {
+                    cudaStream_t st, SimDev& S, Layout& L, long long rec_rows = -1) {
   pct_status rc = check_geometry(ph, g, precision);
   if (rc != PCT_OK) return rc;
-  L = layout_of(ph, g, precision);
+  L = layout_of(ph, g, precision, rec_rows);
   if (!ws || ws_bytes < L.total)
     return fail(PCT_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed", ws_bytes, L.total);
   memset(&S, 0, sizeof(S));
@@ -370,45 +371,61 @@ extern "C" pct_status pct_simulate(const pct_phantom* ph, const pct_geometry* g,
 // ---------------------------------------------------------------------------
 // projectors
 // ---------------------------------------------------------------------------
-extern "C" pct_status pct_forward(const pct_phantom* ph, const pct_geometry* g, const pct_csr* A, int64_t row0,
-                                  int64_t n_rows, const float* x, float* y, void* ws, size_t ws_bytes, void* stream) {
-  cudaStream_t st = (cudaStream_t)stream;
-  if (!x || !y) return fail(PCT_EINVAL, "pct_forward: NULL x or y");
-  if (row0 < 0 || n_rows < 0) return fail(PCT_EINVAL, "negative row range");
-  if (A) {
-    if (!A->row_ptr || !A->col || !A->val) return fail(PCT_EINVAL, "incomplete CSR");
-    if (row0 + n_rows > A->n_rows) return fail(PCT_EINVAL, "row range beyond the CSR");
-    launch_csr_forward((const long long*)A->row_ptr, A->col, A->val, row0, n_rows, x, y, st);
-    return cuda_check("csr forward");
-  }
-  SimDev S;
-  Layout L;
-  pct_status rc = make_sim(ph, g, PCT_PREC_F64, ws, ws_bytes, st, S, L);
+extern "C" pct_status pct_projector_workspace_size(const pct_phantom* ph, const pct_geometry* g, int32_t precision,
+                                                   int64_t max_rows, size_t* bytes) {
+  if (!bytes || max_rows < 0) return fail(PCT_EINVAL, "pct_projector_workspace_size: bad arguments");
+  pct_status rc = check_geometry(ph, g, precision);
   if (rc != PCT_OK) return rc;
-  if (row0 + n_rows > L.rows) return fail(PCT_EINVAL, "row range beyond the geometry");
-  launch_mf_forward_f64(S, row0, n_rows, x, y, st);
-  return cuda_check("matrix-free forward");
+  *bytes = layout_of(ph, g, precision, max_rows).total;
+  return PCT_OK;
 }
 
-extern "C" pct_status pct_adjoint(const pct_phantom* ph, const pct_geometry* g, const pct_csr* A, int64_t row0,
-                                  int64_t n_rows, const float* r, float* gout, void* ws, size_t ws_bytes,
-                                  void* stream) {
-  cudaStream_t st = (cudaStream_t)stream;
-  if (!r || !gout) return fail(PCT_EINVAL, "pct_adjoint: NULL r or g");
-  if (row0 < 0 || n_rows < 0) return fail(PCT_EINVAL, "negative row range");
+namespace {
+
+pct_status project(bool adjoint, const pct_phantom* ph, const pct_geometry* g, const pct_csr* A, int32_t precision,
+                   int64_t row0, int64_t n_rows, const float* in, float* out, void* ws, size_t ws_bytes,
+                   cudaStream_t st) {
+  const char* what = adjoint ? "pct_adjoint" : "pct_forward";
+  if (!in || !out) return fail(PCT_EINVAL, "%s: NULL input or output", what);
+  if (row0 < 0 || n_rows < 0) return fail(PCT_EINVAL, "%s: negative row range", what);
   if (A) {
-    if (!A->row_ptr || !A->col || !A->val) return fail(PCT_EINVAL, "incomplete CSR");
-    if (row0 + n_rows > A->n_rows) return fail(PCT_EINVAL, "row range beyond the CSR");
-    launch_csr_adjoint((const long long*)A->row_ptr, A->col, A->val, row0, n_rows, r, gout, st);
-    return cuda_check("csr adjoint");
+    if (!A->row_ptr || !A->col || !A->val) return fail(PCT_EINVAL, "%s: incomplete CSR", what);
+    if (row0 + n_rows > A->n_rows) return fail(PCT_EINVAL, "%s: row range beyond the CSR", what);
+    if (adjoint)
+      launch_csr_adjoint((const long long*)A->row_ptr, A->col, A->val, row0, n_rows, in, out, st);
+    else
+      launch_csr_forward((const long long*)A->row_ptr, A->col, A->val, row0, n_rows, in, out, st);
+    return cuda_check(what);
   }
   SimDev S;
   Layout L;
-  pct_status rc = make_sim(ph, g, PCT_PREC_F64, ws, ws_bytes, st, S, L);
+  pct_status rc = make_sim(ph, g, precision, ws, ws_bytes, st, S, L, n_rows);
   if (rc != PCT_OK) return rc;
-  if (row0 + n_rows > L.rows) return fail(PCT_EINVAL, "row range beyond the geometry");
-  launch_mf_adjoint_f64(S, row0, n_rows, r, gout, st);
-  return cuda_check("matrix-free adjoint");
+  if (row0 + n_rows > L.rows) return fail(PCT_EINVAL, "%s: row range beyond the geometry", what);
+  if (precision == PCT_PREC_F64) {
+    if (adjoint)
+      launch_mf_adjoint_f64(S, row0, n_rows, in, out, st);
+    else
+      launch_mf_forward_f64(S, row0, n_rows, in, out, st);
+  } else {
+    launch_proj_mixed(adjoint, S, (const char*)ws + L.basis32, row0, n_rows, (char*)ws + L.rec, in, out,
+                      (char*)ws + L.args, st);
+  }
+  return cuda_check(what);
+}
+
+}  // namespace
+
+extern "C" pct_status pct_forward(const pct_phantom* ph, const pct_geometry* g, const pct_csr* A, int32_t precision,
+                                  int64_t row0, int64_t n_rows, const float* x, float* y, void* ws, size_t ws_bytes,
+                                  void* stream) {
+  return project(false, ph, g, A, precision, row0, n_rows, x, y, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" pct_status pct_adjoint(const pct_phantom* ph, const pct_geometry* g, const pct_csr* A, int32_t precision,
+                                  int64_t row0, int64_t n_rows, const float* r, float* gout, void* ws,
+                                  size_t ws_bytes, void* stream) {
+  return project(true, ph, g, A, precision, row0, n_rows, r, gout, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------

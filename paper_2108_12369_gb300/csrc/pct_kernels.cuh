@@ -34,6 +34,11 @@ void launch_count_mixed(const SimDev& S, const void* tab, long long n, void* rec
 void launch_fill_mixed(const SimDev& S, const void* tab, long long n, const void* rec, const long long* row_ptr,
                        const float* x, int* col, float* val, float* b, void* args, cudaStream_t st);
 
+// matrix-free projector, rows [row_base, row_base + n): y = A x (in = x,
+// out = y[n]) or g += A^T r (in = r[n], out = g); rec holds n rows of records
+void launch_proj_mixed(bool adjoint, const SimDev& S, const void* tab, long long row_base, long long n, void* rec,
+                       const float* in, float* out, void* args, cudaStream_t st);
+
 // row pointers (pct_scan.cu): row_ptr[0] = 0, row_ptr[1..n] = inclusive scan
 // of the counts already stored in row_ptr[1..n]; partial holds
 // ceil(n / kScanTile) + 1 int64 of scratch.

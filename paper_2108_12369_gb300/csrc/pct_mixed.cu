@@ -25,6 +25,7 @@ struct MergeToF32 {
 // and read conflict-free) and the warp writes each lane's run with
 // coalesced stores; segments walked in FP64 write straight to global.
 struct CountSinkM {
+  static constexpr bool kStaged = false;
   long long n;
   template <class L>
   __device__ void put(int, L) {
@@ -36,6 +37,7 @@ constexpr int kChunk = 32;     // walk steps between two flushes
 constexpr int kRingPitch = 33;
 
 struct FillSinkR {
+  static constexpr bool kStaged = true;
   int* colb;        // this warp's staging, [kChunk][kRingPitch]
   float* valb;
   int n, lane;      // staged entries of this lane
@@ -85,7 +87,7 @@ struct FillSinkR {
 // all segments of one row.  The segment loop runs to the warp's largest
 // vertex count so that the lanes set up segment q together; walks advance
 // in chunks of kChunk entries, after which the fill kernel flushes.
-template <int DIM, bool kFill, class Sink>
+template <int DIM, bool kLengths, class Sink>
 __device__ __forceinline__ void walk_row_df(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
                                             const RowDF& r, const PathF64* p64, bool live_row, Sink& sink) {
   // r refers to the row record in global memory: its fields are re-read per
@@ -117,22 +119,22 @@ __device__ __forceinline__ void walk_row_df(const SimDev& S, const MixArgs& M, c
     // segments whose direction cannot be certified are walked in FP64
     const bool f64seg = act && res == 2;
     if (__any_sync(0xffffffffu, f64seg)) {
-      if constexpr (kFill) sink.flush();
+      if constexpr (Sink::kStaged) sink.flush();
       if (f64seg) {
-        if constexpr (kFill) sink.direct = true;
+        if constexpr (Sink::kStaged) sink.direct = true;
         double P[3], Q[3];
         path_vertex(*Sg, *p64, q, P);
         path_vertex(*Sg, *p64, q + 1, Q);
         SegF64 s64;
         if (seg_setup_f64(g, P, Q, s64)) seg_walk_f64(g, s64, m64, sink);
-        if constexpr (kFill) sink.direct = false;
+        if constexpr (Sink::kStaged) sink.direct = false;
       }
     }
     const bool walking = act && res == 1;
     Lean<DIM> L;
     const float seglen = sg.L;
     if (walking) lean_begin<DIM>(g, sg, w, q, L);
-    if constexpr (kFill) {
+    if constexpr (kLengths) {
       while (__any_sync(0xffffffffu, walking && !L.done)) {
 #pragma unroll 1
         for (int c = 0; c < kChunk; ++c) {
@@ -142,7 +144,7 @@ __device__ __forceinline__ void walk_row_df(const SimDev& S, const MixArgs& M, c
             mg.emit(vc, l * seglen, sink);
           }
         }
-        sink.flush();
+        if constexpr (Sink::kStaged) sink.flush();
       }
     } else {
       if (walking) {
@@ -160,7 +162,7 @@ __device__ __forceinline__ void walk_row_df(const SimDev& S, const MixArgs& M, c
     }
   }
   if (nv > 0) mg.finish(sink);
-  if constexpr (kFill) sink.flush();
+  if constexpr (Sink::kStaged) sink.flush();
 }
 
 // Rows of one block are regrouped by vertex count (path kind) so that each
@@ -312,6 +314,66 @@ void launch_batch(bool fill, int dim, const BatchInst* B, int n_inst, long long 
   if (!fill && dim == 3) k_batch<false, 3><<<grid, 128, 0, st>>>(B, n_inst, first, last, next);
 }
 
+// ---------------------------------------------------------------------------
+// Matrix-free projectors (rows recomputed, nothing stored): y_i = <a_i, x>
+// or g += a_i r_i, for rows [row_base, row_base + n).  Same paths, same
+// decisions and the same FP32 lengths as the fill.
+// ---------------------------------------------------------------------------
+struct DotSinkM {
+  static constexpr bool kStaged = false;
+  const float* x;
+  float sum, comp;
+  __device__ void put(int c, float len) {
+    float y = len * __ldg(x + c) - comp;
+    float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+  }
+};
+
+struct ScatterSinkM {
+  static constexpr bool kStaged = false;
+  float* g;
+  float r;
+  __device__ void put(int c, float len) { atomicAdd(g + c, len * r); }
+};
+
+template <int DIM, bool kAdjoint>
+__device__ __forceinline__ void proj_block(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
+                                           long long n, long long row0, long long row_base,
+                                           const float* __restrict__ in, float* __restrict__ out) {
+  long long i = row0 + threadIdx.x;
+  int key = -1;
+  if (i < n && (!kAdjoint || in[i] != 0.0f)) {
+    PathF64 p = path_setup(S, row_base + i);
+    M.r64[i] = p;
+    RowDF r;
+    make_rowdf<DIM>(p, S.R, 1.0f, r);
+    M.rdf[i] = r;
+    key = nv_key(p.nv);
+  } else if (i < n && !kAdjoint) {
+    key = -1;
+  }
+  __threadfence_block();
+  long long row = regroup_rows(i, key);
+  const bool live = row >= 0;
+  if constexpr (kAdjoint) {
+    ScatterSinkM sk{out, live ? in[row] : 0.f};
+    walk_row_df<DIM, true>(S, M, Sg, gdg, M.rdf[live ? row : 0], M.r64 + (live ? row : 0), live, sk);
+  } else {
+    DotSinkM sk{in, 0.f, 0.f};
+    walk_row_df<DIM, true>(S, M, Sg, gdg, M.rdf[live ? row : 0], M.r64 + (live ? row : 0), live, sk);
+    if (live) out[row] = sk.sum;
+  }
+}
+
+template <int DIM, bool kAdjoint>
+__global__ void __launch_bounds__(128) k_proj_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
+                                                    long long n, long long row_base, const float* __restrict__ in,
+                                                    float* __restrict__ out) {
+  proj_block<DIM, kAdjoint>(S, M, Sg, gdg, n, (long long)blockIdx.x * blockDim.x, row_base, in, out);
+}
+
 static df split_host(double v) {
   float hi = (float)v;
   return df{hi, (float)(v - (double)hi)};
@@ -387,6 +449,28 @@ void launch_fill_mixed(const SimDev& S, const void* tab, long long n, const void
     k_fill_mixed<2><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n, row_ptr, x, col, val, b);
   else
     k_fill_mixed<3><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n, row_ptr, x, col, val, b);
+}
+
+void launch_proj_mixed(bool adjoint, const SimDev& S, const void* tab, long long row_base, long long n, void* rec,
+                       const float* in, float* out, void* args, cudaStream_t st) {
+  if (n <= 0) return;
+  MixArgs M = mix_args(S, n, tab, rec);
+  const SimDev* Sg;
+  const GridDF* gdg;
+  if (!upload_args(S, M, args, st, &Sg, &gdg)) return;
+  int threads = 128;
+  unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  if (S.ph.g.dim == 2) {
+    if (adjoint)
+      k_proj_mixed<2, true><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n, row_base, in, out);
+    else
+      k_proj_mixed<2, false><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n, row_base, in, out);
+  } else {
+    if (adjoint)
+      k_proj_mixed<3, true><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n, row_base, in, out);
+    else
+      k_proj_mixed<3, false><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n, row_base, in, out);
+  }
 }
 
 size_t mixed_record_size(long long rows) {

@@ -66,7 +66,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 # every symbol include/pct.h declares
 EXPORTS = ["pct_phantom_create", "pct_phantom_destroy", "pct_phantom_nvox", "pct_phantom_rasterize",
            "pct_simulate_workspace_size", "pct_simulate_count", "pct_simulate_fill", "pct_simulate",
-           "pct_forward", "pct_adjoint", "pct_batch_workspace_size", "pct_batch_create",
+           "pct_projector_workspace_size", "pct_forward", "pct_adjoint", "pct_batch_workspace_size", "pct_batch_create",
            "pct_batch_count", "pct_batch_nnz", "pct_batch_fill", "pct_batch_params", "pct_batch_destroy",
            "pct_scan_counts_static", "pct_last_error", "pct_version"]
 BATCH_AUTOTUNE = 1
@@ -93,10 +93,12 @@ def lib():
             "pct_simulate_fill": ([vp, P(Geometry), C.c_int32, vp, C.c_size_t, vp, vp, vp, vp, vp, vp],
                                   C.c_int),
             "pct_simulate": ([vp, P(Geometry), C.c_int32, ALLOC_FN, FREE_FN, vp, P(Csr), vp], C.c_int),
-            "pct_forward": ([vp, P(Geometry), P(Csr), C.c_int64, C.c_int64, vp, vp, vp, C.c_size_t, vp],
-                            C.c_int),
-            "pct_adjoint": ([vp, P(Geometry), P(Csr), C.c_int64, C.c_int64, vp, vp, vp, C.c_size_t, vp],
-                            C.c_int),
+            "pct_projector_workspace_size": ([vp, P(Geometry), C.c_int32, C.c_int64, P(C.c_size_t)],
+                                             C.c_int),
+            "pct_forward": ([vp, P(Geometry), P(Csr), C.c_int32, C.c_int64, C.c_int64, vp, vp, vp,
+                             C.c_size_t, vp], C.c_int),
+            "pct_adjoint": ([vp, P(Geometry), P(Csr), C.c_int32, C.c_int64, C.c_int64, vp, vp, vp,
+                             C.c_size_t, vp], C.c_int),
             "pct_scan_counts_static": ([vp, C.c_int64, vp], C.c_int),
             "pct_batch_workspace_size": ([P(BatchItem), C.c_int32, P(C.c_size_t)], C.c_int),
             "pct_batch_create": ([P(BatchItem), C.c_int32, vp, C.c_size_t, C.c_int32, vp, P(vp)], C.c_int),
@@ -269,18 +271,24 @@ def scan_counts_static(row_ptr, n_rows: int, stream=None):
     _check(lib().pct_scan_counts_static(_ptr(row_ptr), int(n_rows), _stream(stream)))
 
 
-def forward(ph, geo, A, row0, n_rows, x, y, workspace=None, stream=None):
+def projector_workspace_size(ph: Phantom, geo: GeometryArgs, max_rows: int, precision: int = PREC_MIXED) -> int:
+    n = C.c_size_t()
+    _check(lib().pct_projector_workspace_size(ph.handle, C.byref(geo.c), precision, int(max_rows), C.byref(n)))
+    return n.value
+
+
+def forward(ph, geo, A, row0, n_rows, x, y, workspace=None, stream=None, precision=PREC_MIXED):
     """y = A x over rows [row0, row0 + n_rows) (CSR if A is given, else matrix-free)."""
     ws = workspace
-    _check(lib().pct_forward(ph.handle if ph else None, C.byref(geo.c) if geo else None, _csr(A),
+    _check(lib().pct_forward(ph.handle if ph else None, C.byref(geo.c) if geo else None, _csr(A), precision,
                              row0, n_rows, _ptr(x), _ptr(y), _ptr(ws),
                              0 if ws is None else ws.numel() * ws.element_size(), _stream(stream)))
 
 
-def adjoint(ph, geo, A, row0, n_rows, r, g, workspace=None, stream=None):
+def adjoint(ph, geo, A, row0, n_rows, r, g, workspace=None, stream=None, precision=PREC_MIXED):
     """g += A^T r over rows [row0, row0 + n_rows)."""
     ws = workspace
-    _check(lib().pct_adjoint(ph.handle if ph else None, C.byref(geo.c) if geo else None, _csr(A),
+    _check(lib().pct_adjoint(ph.handle if ph else None, C.byref(geo.c) if geo else None, _csr(A), precision,
                              row0, n_rows, _ptr(r), _ptr(g), _ptr(ws),
                              0 if ws is None else ws.numel() * ws.element_size(), _stream(stream)))
 
