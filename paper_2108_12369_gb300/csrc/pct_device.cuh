@@ -344,7 +344,8 @@ __device__ __forceinline__ void path_vertex(const SimDev& S, const PathF64& p, i
 // ---------------------------------------------------------------------------
 // Row assembly: merges the first entry of a segment into the previous
 // entry when it is the same voxel and the previous segment ended there.
-// Sink::put(col, len) receives the merged entries in path order.
+// Sink::put(col, len) receives the merged entries in path order;
+// Sink::pend(col) is told each new pending voxel one step before its put().
 // ---------------------------------------------------------------------------
 template <class Len>
 struct RowMerge {
@@ -369,6 +370,7 @@ struct RowMerge {
     pend_len = len;
     has_pend = true;
     cur_any = true;
+    sink.pend(col);  // lets a sink start loading what put() will need
   }
   __device__ void seg_end() { prev_nonempty = cur_any; }
   template <class Sink>

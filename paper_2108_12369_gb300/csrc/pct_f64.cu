@@ -72,6 +72,7 @@ void launch_raster(const PhantomDev& ph, float* x, long long nvox, cudaStream_t 
 struct CountSink {
   long long n;
   __device__ void put(int, double) { ++n; }
+  __device__ void pend(int) {}
 };
 
 struct FillSinkF64 {
@@ -88,6 +89,7 @@ struct FillSinkF64 {
     ++pos;
     b = b + len * (double)__ldg(x + c);
   }
+  __device__ void pend(int) {}
 };
 
 template <class Sink>
@@ -143,6 +145,7 @@ struct DotSinkF64 {
   const float* x;
   double acc;
   __device__ void put(int c, double len) { acc = acc + len * (double)__ldg(x + c); }
+  __device__ void pend(int) {}
 };
 
 __global__ void k_mf_forward_f64(SimDev S, long long row0, long long n, const float* __restrict__ x,
@@ -159,6 +162,7 @@ struct ScatterSinkF64 {
   float* g;
   float r;
   __device__ void put(int c, double len) { atomicAdd(g + c, (float)len * r); }
+  __device__ void pend(int) {}
 };
 
 __global__ void k_mf_adjoint_f64(SimDev S, long long row0, long long n, const float* __restrict__ r,

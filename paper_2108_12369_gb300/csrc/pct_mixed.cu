@@ -31,6 +31,7 @@ struct CountSinkM {
   __device__ void put(int, L) {
     ++n;
   }
+  __device__ void pend(int) {}
 };
 
 constexpr int kChunk = 32;     // walk steps between two flushes
@@ -46,9 +47,11 @@ struct FillSinkR {
   long long pos;    // next global position of this lane's row
   bool direct;
   const float* x;
+  float xpend;      // x_true of the pending voxel, loaded a step ahead
   float sum, comp;  // Kahan-compensated WEPL
   bool constant;
   float hconst;
+  __device__ void pend(int c) { xpend = __ldg(x + c); }
   __device__ void put(int c, float len) {
     const float v = constant ? hconst : len;
     if (direct) {
@@ -60,7 +63,7 @@ struct FillSinkR {
       valb[n * kRingPitch + lane] = v;
       ++n;
     }
-    float y = len * __ldg(x + c) - comp;
+    float y = len * xpend - comp;
     float t = sum + y;
     comp = (t - sum) - y;
     sum = t;
@@ -243,6 +246,7 @@ __device__ __forceinline__ void fill_block(const SimDev& S, const MixArgs& M, co
   fs.pos = live ? row_ptr[row] : 0;
   fs.direct = false;
   fs.x = x;
+  fs.xpend = 0.f;
   fs.sum = 0.f;
   fs.comp = 0.f;
   fs.constant = S.md.chord == PCT_CHORD_CONSTANT;
@@ -323,8 +327,10 @@ struct DotSinkM {
   static constexpr bool kStaged = false;
   const float* x;
   float sum, comp;
-  __device__ void put(int c, float len) {
-    float y = len * __ldg(x + c) - comp;
+  float xpend;
+  __device__ void pend(int c) { xpend = __ldg(x + c); }
+  __device__ void put(int, float len) {
+    float y = len * xpend - comp;
     float t = sum + y;
     comp = (t - sum) - y;
     sum = t;
@@ -336,6 +342,7 @@ struct ScatterSinkM {
   float* g;
   float r;
   __device__ void put(int c, float len) { atomicAdd(g + c, len * r); }
+  __device__ void pend(int) {}
 };
 
 template <int DIM, bool kAdjoint>
@@ -361,7 +368,7 @@ __device__ __forceinline__ void proj_block(const SimDev& S, const MixArgs& M, co
     ScatterSinkM sk{out, live ? in[row] : 0.f};
     walk_row_df<DIM, true>(S, M, Sg, gdg, M.rdf[live ? row : 0], M.r64 + (live ? row : 0), live, sk);
   } else {
-    DotSinkM sk{in, 0.f, 0.f};
+    DotSinkM sk{in, 0.f, 0.f, 0.f};
     walk_row_df<DIM, true>(S, M, Sg, gdg, M.rdf[live ? row : 0], M.r64 + (live ? row : 0), live, sk);
     if (live) out[row] = sk.sum;
   }
