@@ -168,7 +168,7 @@ pct_status check_geometry(const pct_phantom* ph, const pct_geometry* g, int prec
 }
 
 // rec_rows >= 0 sizes the row records for that many rows (projector chunks)
-Layout layout_of(const pct_phantom*, const pct_geometry* g, int precision, long long rec_rows = -1) {
+Layout layout_of(const pct_phantom* ph, const pct_geometry* g, int precision, long long rec_rows = -1) {
   Layout L;
   L.rows = (long long)g->n_angles * g->paths_per_angle;
   L.K = (g->model.model == PCT_PATH_SPLINE) ? g->model.spline_segments : 1;
@@ -184,7 +184,9 @@ Layout layout_of(const pct_phantom*, const pct_geometry* g, int precision, long 
   L.args = off;
   off = align256(off + mixed_args_bytes());
   L.rec = off;
-  if (precision == PCT_PREC_MIXED) off = align256(off + mixed_record_size(rec_rows >= 0 ? rec_rows : L.rows));
+  if (precision == PCT_PREC_MIXED)
+    off = align256(off + mixed_record_size(rec_rows >= 0 ? rec_rows : L.rows, ph ? ph->desc.dim : 3, g->model.model,
+                                           g->model.spline_segments));
   L.total = off;
   return L;
 }

@@ -1,0 +1,859 @@
+// pct_coop.cuh -- warp-cooperative traversal of one row (PCT_PREC_MIXED).
+//
+// The per-lane walker (walk_row_df) steps through a row one crossing at a
+// time: every step waits for the previous one.  Here a warp works on one
+// row at a time and every crossing is placed on its own:
+//  - count: the row's segments are set up in double-float exactly as for
+//    the per-lane walker (one segment per lane); each axis' number of
+//    crossings inside a segment follows from one certified comparison of the
+//    plane nearest the segment's end with that end.  Per-segment counts,
+//    merges and prefix sums give the row's entry count; a compact record per
+//    segment is kept for the fill;
+//  - fill: the row's crossings are spread over the lanes.  Plane i of axis a
+//    (counted from the segment's start voxel) is crossing number
+//    i + sum_b n_b of its segment, where n_b, the number of axis-b crossings
+//    before it, follows from one certified comparison with the nearest
+//    axis-b plane.  The voxel it enters is the start voxel moved by i + 1
+//    planes along a and n_b planes along every other axis b; the next
+//    crossing (the first of a's next plane and every other axis' first plane
+//    after it) ends the entry, which the lane writes at its CSR position.
+// Where the FP32 bounds cannot decide, the FP64 definition does (out of
+// line).  Decisions, voxel indices, lengths and merges are those of the
+// per-lane walker.  Rows with an exact tie between crossings of different
+// axes, a segment that needs the FP64 walk, more than kSegMax segments or
+// more than kRowCross crossings are handed to the per-lane walker (lane 0
+// of the warp); the count marks them for the fill.
+#pragma once
+#include "pct_walk.cuh"
+
+namespace pct {
+
+constexpr int kRowIrregular = 1 << 8;  // record 0 of a row: the row goes to the per-lane walker
+constexpr int kMergeBit = 1 << 7;      // segment's first entry continues the previous one
+
+// Summary of one set-up segment.  Crossing i of axis a lies at offset
+// fmaf(i, hv[a], ph0[a]) from the segment's grid entry, within
+// cb[a] + 8u * offset of the FP64 definition's value.
+template <int DIM>
+struct alignas(16) SegP {
+  float ph0[DIM], hv[DIM], cb[DIM], rhv[DIM];
+  float send, eend, L, first;  // end offset and its bound, |Q - P|, first entry's length
+  int kn[DIM], cnt[DIM];       // next plane index, crossings counted before the end
+  int col0, out_k, misc;       // misc: status | (out_ax + 1) << 2 | negative steps << 4
+};
+
+constexpr int kStMiss = 0, kStRegular = 1, kStIrregular = 2;
+
+template <int DIM>
+__device__ __forceinline__ SegP<DIM> seg_status_only(int status) {
+  SegP<DIM> o;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    o.ph0[a] = 0.f;
+    o.hv[a] = 1.f;
+    o.cb[a] = 0.f;
+    o.rhv[a] = 1.f;
+    o.kn[a] = 0;
+    o.cnt[a] = 0;
+  }
+  o.send = 0.f;
+  o.eend = 0.f;
+  o.L = 0.f;
+  o.first = 0.f;
+  o.col0 = 0;
+  o.out_k = 0;
+  o.misc = status;
+  return o;
+}
+
+constexpr float kFar = 3e30f;  // offset of an inert axis' planes (never crossed)
+
+// Summary of a set-up segment: per-axis phases and bounds, and the number
+// of each axis' planes strictly before the segment's end (the exit plane of
+// the exit axis by index, every other axis by one certified comparison).
+// A crossing's nearest plane on another axis b is found from its offset
+// divided by hv[b]; the guards keep every offset that enters such a
+// quotient within 1/64 plane spacing of the FP64 definition's value, so the
+// rounded quotient is one of the two planes around the crossing and one
+// certified comparison settles which side it is on.
+template <int DIM>
+__device__ __forceinline__ SegP<DIM> seg_summary(const GridDev& g, const SegDF& sg, const Walk32& w, ExactRef ends) {
+  SegP<DIM> o;
+  int col = 0, stride = 1, neg = 0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    const bool inert = (sg.inert >> a) & 1u;
+    o.ph0[a] = inert ? kFar : w.ph0[a];
+    o.hv[a] = inert ? kFar : w.hv[a];
+    o.cb[a] = inert ? 0.f : fmaf(8.f * kU32, w.ph0[a] + w.hv[a], w.e0[a]);
+    o.rhv[a] = inert ? 0.f : __frcp_rn(w.hv[a]);
+    o.kn[a] = sg.kn[a];
+    col += sg.idx[a] * stride;
+    stride *= g.n[a];
+    if (sg.step[a] < 0) neg |= 1 << a;
+  }
+  o.send = w.send;
+  o.eend = w.esend;
+  o.L = sg.L;
+  o.col0 = col;
+  o.out_k = sg.out.k;
+  bool ok = true;
+  float fmin = w.send, ecr = 0.f;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    int c = 0;
+    if ((sg.inert >> a) & 1u) {
+      c = 0;
+    } else if (sg.out.ax == a) {
+      c = (sg.out.k - sg.kn[a]) * sg.step[a];
+    } else {
+      ok = ok && o.hv[a] >= 64.f * (fmaf(8.f * kU32, w.send + 2.f * o.hv[a], o.cb[a]) + w.esend);
+      const float jf = fminf(fmaxf(rintf((w.send - o.ph0[a]) * o.rhv[a]), -1.f), 1e6f);
+      const float pj = fmaf(jf, o.hv[a], o.ph0[a]);
+      const float d = w.send - pj;
+      const float e = fmaf(8.f * kU32, fabsf(pj), o.cb[a]) + w.esend;
+      const int j = (int)jf;
+      if (d > e)
+        c = j + 1;
+      else if (d < -e)
+        c = j;
+      else
+        c = (exact_cmp(ends, a, sg.kn[a] + sg.step[a] * j, sg.out.ax, sg.out.k) < 0) ? j + 1 : j;
+    }
+    c = c < 0 ? 0 : c;
+    o.cnt[a] = c;
+    if (c > 0) {
+      fmin = fminf(fmin, o.ph0[a]);
+      ecr = fmaxf(ecr, fmaf(8.f * kU32, w.send, o.cb[a]));  // bound of this axis' crossings
+    }
+  }
+  // every other axis' planes near any crossing
+#pragma unroll
+  for (int b = 0; b < DIM; ++b)
+    if (!((sg.inert >> b) & 1u)) ok = ok && o.hv[b] >= 64.f * (ecr + fmaf(8.f * kU32, w.send + 2.f * o.hv[b], o.cb[b]));
+  if (!ok) return seg_status_only<DIM>(kStIrregular);
+  o.first = fmaxf(fmin, 0.f) * sg.L;
+  o.misc = kStRegular | ((sg.out.ax + 1) << 2) | (neg << 4);
+  return o;
+}
+
+struct DF3 {
+  df v[3];
+};
+
+// grid entry / exit in double-float (segments with an end outside the grid
+// or near a plane): out of line, it is rare inside a row
+template <int DIM>
+static __device__ __noinline__ SegP<DIM> prepare_slow(const SimDev* Sg, const GridDF* gdg, DF3 P, DF3 Q, float mag,
+                                                      ExactRef ends) {
+  SegDF sg;
+  Walk32 w;
+  const int res = seg_setup_df<DIM, true>(Sg->ph.g, *gdg, P.v, Q.v, mag, sg, ends);
+  if (res == 0) return seg_status_only<DIM>(kStMiss);
+  if (res != 1) return seg_status_only<DIM>(kStIrregular);
+  walk_from_df<DIM>(sg, w);
+  return seg_summary<DIM>(Sg->ph.g, sg, w, ends);
+}
+
+template <int DIM>
+__device__ __forceinline__ SegP<DIM> seg_prepare(const GridDev& g, const GridDF& gd, const SimDev* Sg,
+                                                 const GridDF* gdg, const df (&P)[3], const df (&Q)[3], float mag,
+                                                 ExactRef ends) {
+  SegDF sg;
+  Walk32 w;
+  if (seg_setup_fast<DIM>(g, gd, P, Q, mag, sg, w)) return seg_summary<DIM>(g, sg, w, ends);
+  DF3 p3, q3;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    p3.v[a] = (a < DIM) ? P[a] : df{0.f, 0.f};
+    q3.v[a] = (a < DIM) ? Q[a] : df{0.f, 0.f};
+  }
+  return prepare_slow<DIM>(Sg, gdg, p3, q3, mag, ends);
+}
+
+// lead segments (vertex 0 -> 1 and nv-2 -> nv-1), two records per row
+template <int DIM>
+__device__ __forceinline__ SegP<DIM>* lead_rec(const MixArgs& M, long long row) {
+  return (SegP<DIM>*)M.lead + 2 * row;
+}
+
+// ---------------------------------------------------------------------------
+// Compact segment record.  The count kernel writes one per segment (row
+// stride: the model's largest segment count); the fill reads them instead
+// of setting the segments up again.  Words (DIM = 2 | 3):
+//   ph0[DIM] hv[DIM] cb[DIM] send L first col0 misc cnt (u16 pairs) cbase ebase
+// cbase / ebase: the segment's first crossing / entry within the row.
+// ---------------------------------------------------------------------------
+template <int DIM>
+struct SegW {
+  static constexpr int PH0 = 0, HV = DIM, CB = 2 * DIM, SEND = 3 * DIM, L = 3 * DIM + 1, FIRST = 3 * DIM + 2,
+                       COL0 = 3 * DIM + 3, MISC = 3 * DIM + 4, CNT = 3 * DIM + 5, CBASE = CNT + (DIM + 1) / 2,
+                       EBASE = CBASE + 1, NV = (EBASE + 4) / 4;  // int4 per record
+};
+
+template <int DIM>
+struct alignas(16) SegG {
+  int4 v[SegW<DIM>::NV];
+};
+
+// the record as registers
+template <int DIM>
+struct SegR {
+  int w[4 * SegW<DIM>::NV];
+  __device__ float f(int k) const { return __int_as_float(w[k]); }
+  __device__ int cnt(int a) const {
+    const int x = w[SegW<DIM>::CNT + (a >> 1)];
+    return (a & 1) ? (int)((unsigned)x >> 16) : (x & 0xffff);
+  }
+  __device__ int C() const {
+    int c = 0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) c += cnt(a);
+    return c;
+  }
+};
+
+template <int DIM>
+__device__ __forceinline__ SegR<DIM> load_seg(const SegG<DIM>& g) {
+  SegR<DIM> r;
+#pragma unroll
+  for (int q = 0; q < SegW<DIM>::NV; ++q) {
+    const int4 v = g.v[q];
+    r.w[4 * q] = v.x;
+    r.w[4 * q + 1] = v.y;
+    r.w[4 * q + 2] = v.z;
+    r.w[4 * q + 3] = v.w;
+  }
+  return r;
+}
+
+template <int DIM>
+__device__ __forceinline__ void store_rec(SegG<DIM>& g, const SegR<DIM>& r) {
+#pragma unroll
+  for (int q = 0; q < SegW<DIM>::NV; ++q) g.v[q] = make_int4(r.w[4 * q], r.w[4 * q + 1], r.w[4 * q + 2], r.w[4 * q + 3]);
+}
+
+template <int DIM>
+__device__ __forceinline__ SegR<DIM> pack_seg(const SegP<DIM>& p) {
+  using W = SegW<DIM>;
+  SegR<DIM> r;
+#pragma unroll
+  for (int k = 0; k < 4 * W::NV; ++k) r.w[k] = 0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    r.w[W::PH0 + a] = __float_as_int(p.ph0[a]);
+    r.w[W::HV + a] = __float_as_int(p.hv[a]);
+    r.w[W::CB + a] = __float_as_int(p.cb[a]);
+    r.w[W::CNT + (a >> 1)] |= (a & 1) ? (p.cnt[a] << 16) : p.cnt[a];
+  }
+  r.w[W::SEND] = __float_as_int(p.send);
+  r.w[W::L] = __float_as_int(p.L);
+  r.w[W::FIRST] = __float_as_int(p.first);
+  r.w[W::COL0] = p.col0;
+  r.w[W::MISC] = p.misc;
+  return r;
+}
+
+constexpr int kSegMax = 64;     // segments of one row handled cooperatively
+constexpr int kRowCross = 4096; // crossings of one row handled cooperatively
+
+template <int DIM>
+struct CoopSmem {
+  SegG<DIM> tab[kSegMax];
+  unsigned bits[kRowCross / 32 + 4];  // segment starts among the row's crossings
+  unsigned char ord[kSegMax];         // k-th segment with crossings
+  int aux[kSegMax];                   // count: first crossing of axes >= 1
+};
+
+template <int DIM>
+__device__ __forceinline__ int dcol_of(const int (&stride)[3], int misc, int a) {
+  int r = stride[0];
+#pragma unroll
+  for (int b = 1; b < DIM; ++b)
+    if (a == b) r = stride[b];
+  return ((misc >> (4 + a)) & 1) ? -r : r;
+}
+
+// plane index of ordinal k of axis a (counted from the segment's start
+// voxel, recovered from its column index)
+template <int DIM>
+__device__ __forceinline__ int plane_of(const GridDev& g, int col0, int misc, int a, int k) {
+  int q = col0, idx = 0;
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+    const int i = (b < DIM - 1) ? q % g.n[b] : q;
+    if (b == a) idx = i;
+    if (b < DIM - 1) q /= g.n[b];
+  }
+  const bool neg = (misc >> (4 + a)) & 1;
+  return neg ? idx - k : idx + 1 + k;
+}
+
+// warp-wide exclusive prefix sum of v; *total receives the sum
+__device__ __forceinline__ int warp_excl_scan(int v, int lane, int* total) {
+  int x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  *total = __shfl_sync(0xffffffffu, x, 31);
+  return x - v;
+}
+
+// Mark in `bits` the start (base[h]) of every segment with a nonzero count
+// and record its ordinal -> segment map; lanes hold segments lane, lane + 32.
+__device__ __forceinline__ void mark_starts(unsigned* bits, unsigned char* ord, int total, const int (&cnt)[2],
+                                            const int (&base)[2], int lane) {
+  const int nwords = (total + 31) / 32 + 1;
+  for (int w = lane; w < nwords; w += 32) bits[w] = 0u;
+  __syncwarp();
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned prev = 0;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const bool on = cnt[h] > 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, on);
+    if (on) {
+      atomicOr(bits + (base[h] >> 5), 1u << (base[h] & 31));
+      ord[prev + __popc(bal & lt)] = (unsigned char)(lane + 32 * h);
+    }
+    prev += __popc(bal);
+  }
+  __syncwarp();
+}
+
+// segment of crossing position p in round p0 (positions p0 .. p0 + 31 lie in
+// bitmap word p0 / 32); ordbase counts the starts of earlier rounds
+__device__ __forceinline__ int seg_at(const unsigned* bits, const unsigned char* ord, int p0, int lane, int& ordbase) {
+  const unsigned word = bits[p0 >> 5];
+  const int k = ordbase + __popc(word & (0xffffffffu >> (31 - lane))) - 1;
+  ordbase += __popc(word);
+  return ord[k < 0 ? 0 : k];
+}
+
+struct Kahan {
+  float sum, comp;
+  __device__ void add(float v) {
+    float y = v - comp;
+    float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+  }
+};
+
+// Direct-write sink for rows handed to the per-lane walker (one live lane).
+struct FillSinkD {
+  int* col;
+  float* val;
+  long long pos, end;  // next position and the end of the row's range
+  const float* x;
+  float xpend;
+  Kahan k;
+  bool constant;
+  float hconst;
+  __device__ void pend(int c) { xpend = __ldg(x + c); }
+  __device__ void put(int c, float len) {
+    if (pos < end) {
+      col[pos] = c;
+      val[pos] = constant ? hconst : len;
+    }
+    ++pos;
+    k.add(len * xpend);
+  }
+};
+
+// A row the cooperative form does not take, walked by lane 0 with the
+// per-lane walker (all lanes call: the walker's segment loop is warp-wide).
+// Out of line so that its registers and code stay off the common path.
+template <int DIM, bool kFill>
+static __device__ __noinline__ void walk_row_lane0(const SimDev* Sg, MixArgs M, long long row,
+                                                   long long* __restrict__ counts, long long rowstart,
+                                                   long long rowend, const float* __restrict__ x,
+                                                   int* __restrict__ col, float* __restrict__ val,
+                                                   float* __restrict__ b) {
+  const int lane = threadIdx.x & 31;
+  const SimDev& S = *Sg;
+  const RowDF& r = M.rdf[row];
+  const PathF64* p64 = M.r64 + row;
+  if constexpr (kFill) {
+    FillSinkD fs;
+    fs.col = col;
+    fs.val = val;
+    fs.pos = rowstart;
+    fs.end = rowend;
+    fs.x = x;
+    fs.xpend = 0.f;
+    fs.k = Kahan{0.f, 0.f};
+    fs.constant = S.md.chord == PCT_CHORD_CONSTANT;
+    fs.hconst = (float)S.ph.g.h[0];
+    walk_row_df<DIM, true>(S, M, Sg, nullptr, r, p64, lane == 0, fs);
+    if (lane == 0) b[row] = fs.k.sum * r.fac;
+  } else {
+    CountSinkM cs{0};
+    walk_row_df<DIM, false>(S, M, Sg, nullptr, r, p64, lane == 0, cs);
+    if (lane == 0) {
+      counts[row] = cs.n;
+      SegG<DIM>* rec = (SegG<DIM>*)M.segg + row * (long long)M.seg_stride;
+      reinterpret_cast<int*>(rec)[SegW<DIM>::MISC] = kRowIrregular;
+    }
+  }
+  __syncwarp();
+}
+
+// One crossing's view of its segment: the crossing's own axis first, the
+// other axes after it in increasing order (selects only, no indexing).
+template <int DIM>
+struct Axes {
+  float p0[DIM], h[DIM], c[DIM];  // phase, spacing and bound constant per axis
+  int n[DIM], dc[DIM], ax[DIM];   // crossings, column step, original axis
+};
+
+template <int DIM>
+__device__ __forceinline__ Axes<DIM> rotate(const SegR<DIM>& R, int a, const int (&stride)[3]) {
+  using W = SegW<DIM>;
+  float p0[DIM], h[DIM], c[DIM];
+  int n[DIM], dc[DIM];
+  const int misc = R.w[W::MISC];
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    p0[k] = R.f(W::PH0 + k);
+    h[k] = R.f(W::HV + k);
+    c[k] = R.f(W::CB + k);
+    n[k] = R.cnt(k);
+    dc[k] = ((misc >> (4 + k)) & 1) ? -stride[k] : stride[k];
+  }
+  Axes<DIM> X;
+  // slot 0: axis a; slots 1..: the others in increasing order
+  int order[DIM];
+  if constexpr (DIM == 2) {
+    order[0] = a;
+    order[1] = 1 - a;
+  } else {
+    order[0] = a;
+    order[1] = a == 0 ? 1 : 0;
+    order[2] = a == 2 ? 1 : 2;
+  }
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    const int o = order[k];
+    X.p0[k] = pick<DIM>(p0, o);
+    X.h[k] = pick<DIM>(h, o);
+    X.c[k] = pick<DIM>(c, o);
+    X.n[k] = pick<DIM>(n, o);
+    X.dc[k] = pick<DIM>(dc, o);
+    X.ax[k] = o;
+  }
+  return X;
+}
+
+// axis of crossing number l of a segment (axes in order, crossings of each
+// axis consecutive) and its ordinal on that axis
+template <int DIM>
+__device__ __forceinline__ void axis_of(const SegR<DIM>& R, int lo, int l, int& a, int& i) {
+  a = lo;
+  i = l;
+#pragma unroll
+  for (int t = 0; t < DIM - 1; ++t) {
+    if (t < lo) continue;
+    const int c = R.cnt(t);
+    const bool up = a == t && i >= c;
+    i = up ? i - c : i;
+    a = up ? t + 1 : a;
+  }
+}
+
+struct Cross {
+  int rank;   // position among the segment's crossings
+  int colv;   // voxel entered
+  float nv;   // offset of the next crossing (the segment's end after the last)
+  bool last;
+};
+
+// Crossing i of axis X.ax[0].  Common path: every decision taken from the
+// FP32 bounds; *unsure is set where they cannot decide (the caller then
+// uses cross_exact).  The next crossing is the first of: this axis' next
+// plane, every other axis' first plane after the crossing.
+template <int DIM>
+__device__ __forceinline__ Cross cross_fast(const Axes<DIM>& X, int i, int col0, float send, float& ph, bool& unsure) {
+  Cross o;
+  ph = fmaf((float)i, X.h[0], X.p0[0]);
+  o.rank = i;
+  o.colv = col0 + (i + 1) * X.dc[0];
+  bool has = i + 1 < X.n[0];
+  float vm = fmaf((float)(i + 1), X.h[0], X.p0[0]), cm = X.c[0];
+#pragma unroll
+  for (int k = 1; k < DIM; ++k) {
+    const float jf = rintf(__fdividef(ph - X.p0[k], X.h[k]));
+    const float pb = fmaf(jf, X.h[k], X.p0[k]);
+    const float d = ph - pb;
+    const int j = (int)jf;
+    // the clamp below settles candidates outside the counted planes
+    unsure = unsure || (j >= 0 && j < X.n[k] && !(fabsf(d) > fmaf(8.f * kU32, ph + fabsf(pb), X.c[0] + X.c[k])));
+    int nb = j + (d > 0.f ? 1 : 0);
+    nb = nb < 0 ? 0 : (nb > X.n[k] ? X.n[k] : nb);
+    o.rank += nb;
+    o.colv += nb * X.dc[k];
+    if (nb < X.n[k]) {
+      const float v = fmaf((float)nb, X.h[k], X.p0[k]);
+      if (has) {
+        const float d2 = v - vm;
+        unsure = unsure || !(fabsf(d2) > fmaf(8.f * kU32, v + vm, X.c[k] + cm));
+        vm = d2 < 0.f ? v : vm;
+        cm = d2 < 0.f ? X.c[k] : cm;
+      } else {
+        vm = v;
+        cm = X.c[k];
+      }
+      has = true;
+    }
+  }
+  o.last = !has;
+  o.nv = has ? vm : send;
+  return o;
+}
+
+// The same crossing with every decision exact: FP64 comparisons where the
+// FP32 bounds cannot decide (a few crossings per thousand rows).
+template <int DIM>
+static __device__ __noinline__ Cross cross_exact(const SimDev* Sg, const PathF64* p64, int s, Axes<DIM> X, int i,
+                                                 int col0, int misc, float send) {
+  const GridDev& g = Sg->ph.g;
+  const ExactRef ref{Sg, p64, s};
+  Cross o;
+  const float ph = fmaf((float)i, X.h[0], X.p0[0]);
+  const int a = X.ax[0];
+  o.rank = i;
+  o.colv = col0 + (i + 1) * X.dc[0];
+  int mk = i + 1 < X.n[0] ? 0 : -1, mi = i + 1;
+  float vm = fmaf((float)(i + 1), X.h[0], X.p0[0]), cm = X.c[0];
+  for (int k = 1; k < DIM; ++k) {
+    const int c = X.ax[k];
+    const float jf = rintf(__fdividef(ph - X.p0[k], X.h[k]));
+    const float pb = fmaf(jf, X.h[k], X.p0[k]);
+    const float d = ph - pb;
+    const float e = fmaf(8.f * kU32, ph + fabsf(pb), X.c[0] + X.c[k]);
+    const int j = (int)jf;
+    int nb;
+    if (d > e || j < 0 || j >= X.n[k])
+      nb = d > 0.f ? j + 1 : j;
+    else if (d < -e)
+      nb = j;
+    else
+      nb = exact_cmp(ref, a, plane_of<DIM>(g, col0, misc, a, i), c, plane_of<DIM>(g, col0, misc, c, j)) > 0 ? j + 1
+                                                                                                              : j;
+    nb = nb < 0 ? 0 : (nb > X.n[k] ? X.n[k] : nb);
+    o.rank += nb;
+    o.colv += nb * X.dc[k];
+    if (nb < X.n[k]) {
+      const float v = fmaf((float)nb, X.h[k], X.p0[k]);
+      bool take = mk < 0;
+      if (!take) {
+        const float d2 = v - vm;
+        const float e2 = fmaf(8.f * kU32, v + vm, X.c[k] + cm);
+        if (d2 < -e2)
+          take = true;
+        else if (!(d2 > e2))
+          take = exact_cmp(ref, c, plane_of<DIM>(g, col0, misc, c, nb), X.ax[mk],
+                           plane_of<DIM>(g, col0, misc, X.ax[mk], mi)) < 0;
+      }
+      if (take) {
+        mk = k;
+        mi = nb;
+        vm = v;
+        cm = X.c[k];
+      }
+    }
+  }
+  o.last = mk < 0;
+  o.nv = mk < 0 ? send : vm;
+  return o;
+}
+
+// Is crossing i of axis X.ax[0] exactly tied with a plane of an axis below
+// it?  Common path from the FP32 bounds; *unsure where they cannot decide.
+template <int DIM>
+__device__ __forceinline__ void tie_fast(const Axes<DIM>& X, int i, bool& unsure) {
+  const float ph = fmaf((float)i, X.h[0], X.p0[0]);
+#pragma unroll
+  for (int k = 1; k < DIM; ++k) {
+    if (X.ax[k] > X.ax[0]) continue;
+    const float jf = rintf(__fdividef(ph - X.p0[k], X.h[k]));
+    const float pb = fmaf(jf, X.h[k], X.p0[k]);
+    const int j = (int)jf;
+    unsure = unsure || (j >= 0 && j < X.n[k] && !(fabsf(ph - pb) > fmaf(8.f * kU32, ph + fabsf(pb), X.c[0] + X.c[k])));
+  }
+}
+
+template <int DIM>
+static __device__ __noinline__ bool tie_exact(const SimDev* Sg, const PathF64* p64, int s, Axes<DIM> X, int i,
+                                              int col0, int misc) {
+  const GridDev& g = Sg->ph.g;
+  const ExactRef ref{Sg, p64, s};
+  const float ph = fmaf((float)i, X.h[0], X.p0[0]);
+  bool tie = false;
+  for (int k = 1; k < DIM; ++k) {
+    if (X.ax[k] > X.ax[0]) continue;
+    const float jf = rintf(__fdividef(ph - X.p0[k], X.h[k]));
+    const float pb = fmaf(jf, X.h[k], X.p0[k]);
+    const int j = (int)jf;
+    if (j >= 0 && j < X.n[k] && !(fabsf(ph - pb) > fmaf(8.f * kU32, ph + fabsf(pb), X.c[0] + X.c[k])))
+      tie = tie || exact_cmp(ref, X.ax[0], plane_of<DIM>(g, col0, misc, X.ax[0], i), X.ax[k],
+                             plane_of<DIM>(g, col0, misc, X.ax[k], (int)jf)) == 0;
+  }
+  return tie;
+}
+
+// length added to the last entry of segment s by the first entries of the
+// segments after it that continue its voxel
+template <int DIM>
+__device__ __forceinline__ float chain_after(const CoopSmem<DIM>& sm, int s, int nseg, float v) {
+  using W = SegW<DIM>;
+  for (int t = s + 1; t < nseg; ++t) {
+    const int* wt = reinterpret_cast<const int*>(&sm.tab[t]);
+    if (!(wt[W::MISC] & kMergeBit)) break;
+    v = v + __int_as_float(wt[W::FIRST]);
+    const int c01 = wt[W::CNT];
+    const int ct = (c01 & 0xffff) + ((unsigned)c01 >> 16) + (DIM > 2 ? wt[W::CNT + 1] & 0xffff : 0);
+    if (ct > 0) break;
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Count: one row, the whole warp.  Sets up the interior segments (one per
+// lane), forms the per-segment counts, merges and prefix sums, looks for
+// exact ties between crossings of different axes, writes the compact
+// segment records and the row's entry count.
+// ---------------------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ void coop_count_row(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
+                                               long long row, CoopSmem<DIM>& sm, long long* __restrict__ counts) {
+  using W = SegW<DIM>;
+  const int lane = threadIdx.x & 31;
+  const GridDev& g = S.ph.g;
+  const RowDF& r = M.rdf[row];
+  const int nseg = r.nv - 1;
+  const int stride[3] = {1, g.n[0], g.n[0] * (DIM > 2 ? g.n[1] : 1)};
+  const PathF64* p64 = M.r64 + row;
+  bool irregular = nseg > kSegMax || nseg < 1 || nseg > M.seg_stride;
+  if (!irregular) {
+    // 1. segment table: lead segments from the pre-pass, interior ones here
+    const SegP<DIM>* lead = lead_rec<DIM>(M, row);
+    if (lane < 2 && (lane == 0 || nseg > 1)) {
+      const SegP<DIM> p = lead[lane];
+      const int s = lane == 0 ? 0 : nseg - 1;
+      store_rec<DIM>(sm.tab[s], pack_seg<DIM>(p));
+    }
+    const int nint = nseg - 2;
+    const float mag = r.mag;
+    for (int base = 0; base < nint; base += 32) {
+      const int j = base + lane;
+      df V[3], Vn[3];
+      if (j <= nint) vertex_df<DIM>(r, M.tab, M.R, 1 + j, V);
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        Vn[a].hi = __shfl_down_sync(0xffffffffu, V[a].hi, 1);
+        Vn[a].lo = __shfl_down_sync(0xffffffffu, V[a].lo, 1);
+      }
+      if (lane == 31 && j < nint) vertex_df<DIM>(r, M.tab, M.R, 2 + j, Vn);
+      if (j < nint) {
+        const SegP<DIM> p = seg_prepare<DIM>(g, M.gd, Sg, gdg, V, Vn, mag, ExactRef{Sg, p64, 1 + j});
+        store_rec<DIM>(sm.tab[1 + j], pack_seg<DIM>(p));
+      }
+    }
+    __syncwarp();
+
+    // 2. per-segment crossings, merges, entries; prefix sums
+    int bad = 0, merge[2] = {0, 0}, Cs[2] = {0, 0}, Cen[2] = {0, 0}, Es[2] = {0, 0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int s = lane + 32 * h;
+      if (s < nseg) {
+        const SegR<DIM> R = load_seg<DIM>(sm.tab[s]);
+        const int st = R.w[W::MISC] & 3;
+        int m = 0;
+        if (s > 0 && st == kStRegular) {
+          const SegR<DIM> Q = load_seg<DIM>(sm.tab[s - 1]);
+          if ((Q.w[W::MISC] & 3) == kStRegular) {
+            int colx = Q.w[W::COL0];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) colx += Q.cnt(a) * dcol_of<DIM>(stride, Q.w[W::MISC], a);
+            m = colx == R.w[W::COL0];
+          }
+        }
+        Cs[h] = R.C();
+        Cen[h] = Cs[h] - R.cnt(0);  // the tie search enumerates crossings of axes >= 1
+        Es[h] = (st == kStRegular) ? Cs[h] + 1 - m : 0;
+        merge[h] = m;
+        bad |= st == kStIrregular;
+      }
+    }
+    int t0, t1, cb[2], eb[2], ben[2];
+    cb[0] = warp_excl_scan(Cs[0], lane, &t0);
+    cb[1] = warp_excl_scan(Cs[1], lane, &t1) + t0;
+    const int totC = t0 + t1;
+    eb[0] = warp_excl_scan(Es[0], lane, &t0);
+    eb[1] = warp_excl_scan(Es[1], lane, &t1) + t0;
+    const int totE = t0 + t1;
+    ben[0] = warp_excl_scan(Cen[0], lane, &t0);
+    ben[1] = warp_excl_scan(Cen[1], lane, &t1) + t0;
+    const int totEn = t0 + t1;
+    bad |= totC > kRowCross;
+    irregular = __any_sync(0xffffffffu, bad) != 0;
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int s = lane + 32 * h;
+      if (s < nseg) {
+        int* ws = reinterpret_cast<int*>(&sm.tab[s]);
+        if (merge[h]) ws[W::MISC] |= kMergeBit;
+        ws[W::CBASE] = cb[h];
+        ws[W::EBASE] = eb[h];
+      }
+    }
+    __syncwarp();
+
+    // 3. exact ties between crossings of different axes (each crossing of
+    // axis a >= 1 against the nearest planes of the axes below it)
+    if (!irregular) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (lane + 32 * h < nseg) sm.aux[lane + 32 * h] = ben[h];
+      bool tie = false;
+      mark_starts(sm.bits, sm.ord, totEn, Cen, ben, lane);
+      int ordbase = 0;
+      for (int p0 = 0; p0 < totEn; p0 += 32) {
+        const int s = seg_at(sm.bits, sm.ord, p0, lane, ordbase);
+        const int p = p0 + lane;
+        if (p < totEn) {
+          const SegR<DIM> R = load_seg<DIM>(sm.tab[s]);
+          int a, i;
+          axis_of<DIM>(R, 1, p - sm.aux[s], a, i);
+          const Axes<DIM> X = rotate<DIM>(R, a, stride);
+          bool unsure = false;
+          tie_fast<DIM>(X, i, unsure);
+          if (unsure) tie = tie || tie_exact<DIM>(Sg, p64, s, X, i, R.w[W::COL0], R.w[W::MISC]);
+        }
+      }
+      irregular = __any_sync(0xffffffffu, tie) != 0;
+    }
+    if (!irregular) {
+      SegG<DIM>* dst = (SegG<DIM>*)M.segg + row * (long long)M.seg_stride;
+      const int4* src = reinterpret_cast<const int4*>(sm.tab);
+      int4* d4 = reinterpret_cast<int4*>(dst);
+      for (int q = lane; q < nseg * W::NV; q += 32) d4[q] = src[q];
+      if (lane == 0) counts[row] = totE;
+      __syncwarp();
+      return;
+    }
+  }
+  walk_row_lane0<DIM, false>(Sg, M, row, counts, 0, 0, nullptr, nullptr, nullptr, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Fill: one row, the whole warp, from the count's segment records.  Each
+// lane takes one crossing: its position in the segment, the voxel it
+// enters and the next crossing (own axis' next plane or another axis' first
+// plane after it, certified like the position) give one entry, written at
+// its CSR position; entry 0 of every segment comes from the segment's lane.
+// ---------------------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ void coop_fill_row(const SimDev& S, const MixArgs& M, const SimDev* Sg, long long row,
+                                              CoopSmem<DIM>& sm, const long long* __restrict__ row_ptr,
+                                              const float* __restrict__ x, int* __restrict__ col,
+                                              float* __restrict__ val, float* __restrict__ b) {
+  using W = SegW<DIM>;
+  const int lane = threadIdx.x & 31;
+  const GridDev& g = S.ph.g;
+  const RowDF& r = M.rdf[row];
+  const int nseg = r.nv - 1;
+  const long long rowstart = row_ptr[row], rowend = row_ptr[row + 1];
+  const SegG<DIM>* rec = (const SegG<DIM>*)M.segg + row * (long long)M.seg_stride;
+  bool irregular = nseg > kSegMax || nseg < 1 || nseg > M.seg_stride;
+  if (!irregular) irregular = (reinterpret_cast<const int*>(rec)[W::MISC] & kRowIrregular) != 0;
+  if (!irregular) {
+    const int stride[3] = {1, g.n[0], g.n[0] * (DIM > 2 ? g.n[1] : 1)};
+    const int nvox = g.n[0] * g.n[1] * (DIM > 2 ? g.n[2] : 1);
+    const int4* src = reinterpret_cast<const int4*>(rec);
+    int4* d4 = reinterpret_cast<int4*>(sm.tab);
+    for (int q = lane; q < nseg * W::NV; q += 32) d4[q] = src[q];
+    __syncwarp();
+    int Cs[2] = {0, 0}, cbase[2] = {0, 0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int s = lane + 32 * h;
+      if (s < nseg) {
+        const SegR<DIM> R = load_seg<DIM>(sm.tab[s]);
+        Cs[h] = R.C();
+        cbase[h] = R.w[W::CBASE];
+      }
+    }
+    const int totC = __reduce_add_sync(0xffffffffu, Cs[0] + Cs[1]);
+    if (totC <= kRowCross) {
+      mark_starts(sm.bits, sm.ord, totC, Cs, cbase, lane);
+      Kahan wk{0.f, 0.f};
+      const bool constant = S.md.chord == PCT_CHORD_CONSTANT;
+      const float hconst = (float)g.h[0];
+      const PathF64* p64 = M.r64 + row;
+      int ordbase = 0;
+      for (int p0 = 0; p0 < totC; p0 += 32) {
+        const int s = seg_at(sm.bits, sm.ord, p0, lane, ordbase);
+        const int p = p0 + lane;
+        if (p < totC) {
+          const SegR<DIM> R = load_seg<DIM>(sm.tab[s]);
+          const int misc = R.w[W::MISC], col0 = R.w[W::COL0];
+          const float send = R.f(W::SEND);
+          int a, i;
+          axis_of<DIM>(R, 0, p - R.w[W::CBASE], a, i);
+          const Axes<DIM> X = rotate<DIM>(R, a, stride);
+          bool unsure = false;
+          float ph;
+          Cross cr = cross_fast<DIM>(X, i, col0, send, ph, unsure);
+          if (unsure) cr = cross_exact<DIM>(Sg, p64, s, X, i, col0, misc, send);
+          float v = fmaxf(cr.nv - ph, 0.f) * R.f(W::L);
+          if (cr.last) v = chain_after<DIM>(sm, s, nseg, v);
+          const long long o = rowstart + R.w[W::EBASE] + cr.rank + 1 - ((misc & kMergeBit) ? 1 : 0);
+          if (o < rowend) {
+            col[o] = cr.colv;
+            val[o] = constant ? hconst : v;
+          }
+          wk.add(v * __ldg(x + ((unsigned)cr.colv < (unsigned)nvox ? cr.colv : 0)));
+        }
+      }
+      // entry 0 of every segment that does not continue the previous one
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int s = lane + 32 * h;
+        if (s < nseg) {
+          const SegR<DIM> R = load_seg<DIM>(sm.tab[s]);
+          const int misc = R.w[W::MISC];
+          if ((misc & 3) == kStRegular && !(misc & kMergeBit)) {
+            float v = R.f(W::FIRST);
+            if (R.C() == 0) v = chain_after<DIM>(sm, s, nseg, v);
+            const int c0 = R.w[W::COL0];
+            const long long o = rowstart + R.w[W::EBASE];
+            if (o < rowend) {
+              col[o] = c0;
+              val[o] = constant ? hconst : v;
+            }
+            wk.add(v * __ldg(x + ((unsigned)c0 < (unsigned)nvox ? c0 : 0)));
+          }
+        }
+      }
+      // the lanes' Kahan partials, summed as double-float
+      df sum = two_sum(wk.sum, -wk.comp);
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) {
+        df o{__shfl_xor_sync(0xffffffffu, sum.hi, d), __shfl_xor_sync(0xffffffffu, sum.lo, d)};
+        sum = df_add(sum, o);
+      }
+      if (lane == 0) b[row] = (sum.hi + sum.lo) * r.fac;
+      __syncwarp();
+      return;
+    }
+  }
+  walk_row_lane0<DIM, true>(Sg, M, row, nullptr, rowstart, rowend, x, col, val, b);
+}
+
+}  // namespace pct

@@ -24,7 +24,9 @@ void launch_mf_adjoint_f64(const SimDev& S, long long row0, long long n, const f
 // double-float certified form (pct_mixed.cu).  rec: per-row records
 // (mixed_record_size bytes); tab: Hermite basis table (basis_df_bytes(K + 1)
 // bytes, filled on the host by fill_basis_df from s, h10, h11 at j = 0..K).
-size_t mixed_record_size(long long rows);
+size_t mixed_record_size(long long rows, int dim, int model, int K);
+// compact segment records per row (the model's largest segment count, capped)
+int seg_stride_of(int model, int K);
 size_t mixed_args_bytes();
 size_t basis_df_bytes(int n);
 void fill_basis_df(const double* s, const double* h10, const double* h11, int n, void* host_out);

@@ -1,204 +1,41 @@
 // pct_mixed.cu -- PCT_PREC_MIXED kernels.
-//   count: FP64 path set-up once per proton (the definition), kept as two row
-//          records (FP64 for exact decisions, double-float for the walk);
-//          double-float certified traversal -> entries per row.
-//   fill:  double-float traversal from the record -> col / val in path order,
-//          FP32 Kahan-compensated WEPL, noise factor.
+//   count: FP64 path set-up once per proton (the definition), kept as row
+//          records (FP64 for exact decisions, double-float for the set-up);
+//          warp-cooperative set-up of every segment -> entries per row and
+//          compact segment records.
+//   fill:  warp-cooperative placement of every crossing from the segment
+//          records -> col / val in path order, FP32 Kahan-compensated WEPL
+//          per lane summed in double-float, noise factor.
+//   batch: one persistent launch of either phase over many simulations.
+//   projectors: matrix-free y = A x / g += A^T r with the per-lane walker.
 #include "pct_kernels.cuh"
-#include "pct_mixed.cuh"
+#include "pct_coop.cuh"
 
 namespace pct {
 
 
-// feeds FP64-walked entries into the FP32 row merge
-template <class M>
-struct MergeToF32 {
-  M* mg;
-  template <class Sink>
-  __device__ void emit(int col, double len, Sink& sink) {
-    mg->emit(col, (float)len, sink);
-  }
-};
-
-// Finished entries of a row.  The count kernel only counts them.  The fill
-// kernel stages them per lane in shared memory ([k][33] layout: lanes write
-// and read conflict-free) and the warp writes each lane's run with
-// coalesced stores; segments walked in FP64 write straight to global.
-struct CountSinkM {
-  static constexpr bool kStaged = false;
-  long long n;
-  template <class L>
-  __device__ void put(int, L) {
-    ++n;
-  }
-  __device__ void pend(int) {}
-};
-
-constexpr int kChunk = 32;     // walk steps between two flushes
-constexpr int kRingPitch = 33;
-
-struct FillSinkR {
-  static constexpr bool kStaged = true;
-  int* colb;        // this warp's staging, [kChunk][kRingPitch]
-  float* valb;
-  int n, lane;      // staged entries of this lane
-  int* col;
-  float* val;
-  long long pos;    // next global position of this lane's row
-  bool direct;
-  const float* x;
-  float xpend;      // x_true of the pending voxel, loaded a step ahead
-  float sum, comp;  // Kahan-compensated WEPL
-  bool constant;
-  float hconst;
-  __device__ void pend(int c) { xpend = __ldg(x + c); }
-  __device__ void put(int c, float len) {
-    const float v = constant ? hconst : len;
-    if (direct) {
-      col[pos] = c;
-      val[pos] = v;
-      ++pos;
-    } else {
-      colb[n * kRingPitch + lane] = c;
-      valb[n * kRingPitch + lane] = v;
-      ++n;
-    }
-    float y = len * xpend - comp;
-    float t = sum + y;
-    comp = (t - sum) - y;
-    sum = t;
-  }
-  // warp-cooperative: every lane's staged run goes to its row
-  __device__ void flush() {
-    unsigned todo = __ballot_sync(0xffffffffu, n > 0);
-    while (todo) {
-      const int L = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const int nL = __shfl_sync(0xffffffffu, n, L);
-      const long long pL = __shfl_sync(0xffffffffu, pos, L);
-      if (lane < nL) {
-        col[pL + lane] = colb[lane * kRingPitch + L];
-        val[pL + lane] = valb[lane * kRingPitch + L];
-      }
-    }
-    pos += n;
-    n = 0;
-    __syncwarp();
-  }
-};
-
-// all segments of one row.  The segment loop runs to the warp's largest
-// vertex count so that the lanes set up segment q together; walks advance
-// in chunks of kChunk entries, after which the fill kernel flushes.
-template <int DIM, bool kLengths, class Sink>
-__device__ __forceinline__ void walk_row_df(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
-                                            const RowDF& r, const PathF64* p64, bool live_row, Sink& sink) {
-  // r refers to the row record in global memory: its fields are re-read per
-  // segment (L1 hits) instead of occupying ~40 registers for the whole row
-  const GridDev& g = S.ph.g;
-  const float mag = live_row ? r.mag : 0.f;
-  RowMerge<float> mg;
-  mg.init();
-  MergeToF32<RowMerge<float>> m64{&mg};
-  const int nv = live_row ? r.nv : 0;
-  const int nv_max = __reduce_max_sync(0xffffffffu, nv);
-  df Va[3], Vb[3];
-  if (nv > 0) vertex_df<DIM>(r, M.tab, M.R, 0, Va);
-  for (int q = 0; q + 1 < nv_max; ++q) {
-    const bool act = q + 1 < nv;
-    int res = 0;
-    SegDF sg;
-    Walk32 w;
-    ExactRef ends{Sg, p64, q};
-    if (act) {
-      vertex_df<DIM>(r, M.tab, M.R, q + 1, Vb);
-      mg.seg_begin();
-      res = 1;
-      if (!seg_setup_fast<DIM>(g, M.gd, Va, Vb, mag, sg, w)) {
-        res = seg_setup_df<DIM>(g, M.gd, Va, Vb, mag, sg, ends);
-        if (res == 1) walk_from_df<DIM>(sg, w);
-      }
-    }
-    // segments whose direction cannot be certified are walked in FP64
-    const bool f64seg = act && res == 2;
-    if (__any_sync(0xffffffffu, f64seg)) {
-      if constexpr (Sink::kStaged) sink.flush();
-      if (f64seg) {
-        if constexpr (Sink::kStaged) sink.direct = true;
-        double P[3], Q[3];
-        path_vertex(*Sg, *p64, q, P);
-        path_vertex(*Sg, *p64, q + 1, Q);
-        SegF64 s64;
-        if (seg_setup_f64(g, P, Q, s64)) seg_walk_f64(g, s64, m64, sink);
-        if constexpr (Sink::kStaged) sink.direct = false;
-      }
-    }
-    const bool walking = act && res == 1;
-    Lean<DIM> L;
-    const float seglen = sg.L;
-    if (walking) lean_begin<DIM>(g, sg, w, q, L);
-    if constexpr (kLengths) {
-      while (__any_sync(0xffffffffu, walking && !L.done)) {
-#pragma unroll 1
-        for (int c = 0; c < kChunk; ++c) {
-          if (walking && !L.done) {
-            const int vc = L.col;
-            const float l = lean_step<DIM>(L, r, M.tab, M.R, M.gd, g, mag, ends);
-            mg.emit(vc, l * seglen, sink);
-          }
-        }
-        if constexpr (Sink::kStaged) sink.flush();
-      }
-    } else {
-      if (walking) {
-        while (!L.done) {
-          const int vc = L.col;
-          lean_step<DIM>(L, r, M.tab, M.R, M.gd, g, mag, ends);
-          mg.emit(vc, 0.f, sink);
-        }
-      }
-    }
-    if (act) {
-      mg.seg_end();
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) Va[a] = Vb[a];
-    }
-  }
-  if (nv > 0) mg.finish(sink);
-  if constexpr (Sink::kStaged) sink.flush();
+template <int DIM>
+__device__ __forceinline__ CoopSmem<DIM>& coop_smem() {
+  extern __shared__ __align__(16) unsigned char coop_dyn[];
+  return reinterpret_cast<CoopSmem<DIM>*>(coop_dyn)[threadIdx.x >> 5];
 }
 
-// Rows of one block are regrouped by vertex count (path kind) so that each
-// warp walks rows with the same number of segments.  Returns the row this
-// thread processes (or -1).  key: 0, 1, 2 for 2, 4, more vertices.
-__device__ __forceinline__ long long regroup_rows(long long row, int key) {
-  __shared__ int cnt[3];
-  __shared__ int perm[128];
-  if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
-  __syncthreads();
-  int slot = -1;
-  if (key >= 0) slot = atomicAdd(&cnt[key], 1);
-  __syncthreads();
-  if (key >= 0) {
-    int base = (key > 0 ? cnt[0] : 0) + (key > 1 ? cnt[1] : 0);
-    perm[base + slot] = threadIdx.x;
-  }
-  int total = cnt[0] + cnt[1] + cnt[2];
-  __syncthreads();
-  long long block0 = row - threadIdx.x;
-  return (threadIdx.x < total) ? block0 + perm[threadIdx.x] : -1;
+// dynamic shared memory of a 128-thread count / fill block
+template <int DIM, bool kFill>
+constexpr size_t coop_bytes() {
+  return 4 * sizeof(CoopSmem<DIM>);
 }
 
-__device__ __forceinline__ int nv_key(int nv) { return nv <= 2 ? 0 : (nv <= 4 ? 1 : 2); }
-
-// One block of 128 consecutive rows starting at row0 (count phase).  The
+// One block of 128 consecutive rows starting at row0 (count phase).  Thread
+// t forms the FP64 path of row row0 + t (the definition), keeps it and its
+// double-float copy as row records and sets up the row's lead-in and
+// lead-out segments; then each warp counts its 32 rows one at a time.  The
 // arguments may live in parameter space (one launch per simulation) or in
 // global memory (the batch kernel).
 template <int DIM>
 __device__ __forceinline__ void count_block(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
                                             long long n, long long row0, long long* __restrict__ counts) {
-  long long i = row0 + threadIdx.x;
-  int key = -1;
+  const long long i = row0 + threadIdx.x;
   if (i < n) {
     PathF64 p = path_setup(S, i);
     M.r64[i] = p;  // exact decisions read the FP64 path back from here
@@ -206,57 +43,51 @@ __device__ __forceinline__ void count_block(const SimDev& S, const MixArgs& M, c
     RowDF r;
     make_rowdf<DIM>(p, S.R, fac, r);
     M.rdf[i] = r;
-    key = nv_key(p.nv);
+    SegP<DIM>* lead = lead_rec<DIM>(M, i);
+    df Va[3], Vb[3];
+    vertex_df<DIM>(r, M.tab, M.R, 0, Va);
+    vertex_df<DIM>(r, M.tab, M.R, 1, Vb);
+    lead[0] = seg_prepare<DIM>(S.ph.g, M.gd, Sg, gdg, Va, Vb, r.mag, ExactRef{Sg, M.r64 + i, 0});
+    if (r.nv > 2) {
+      vertex_df<DIM>(r, M.tab, M.R, r.nv - 2, Va);
+      vertex_df<DIM>(r, M.tab, M.R, r.nv - 1, Vb);
+      lead[1] = seg_prepare<DIM>(S.ph.g, M.gd, Sg, gdg, Va, Vb, r.mag, ExactRef{Sg, M.r64 + i, r.nv - 2});
+    }
   }
-  __threadfence_block();
-  long long row = regroup_rows(i, key);
-  const bool live = row >= 0;
-  CountSinkM cs{0};
-  walk_row_df<DIM, false>(S, M, Sg, gdg, M.rdf[live ? row : 0], M.r64 + (live ? row : 0), live, cs);
-  if (live) counts[row] = cs.n;
+  __syncwarp();  // the warp's 32 row records are complete
+  CoopSmem<DIM>& sm = coop_smem<DIM>();
+  const long long w0 = row0 + (threadIdx.x & ~31u);
+  for (int j = 0; j < 32; ++j) {
+    const long long row = w0 + j;
+    if (row >= n) break;
+    coop_count_row<DIM>(S, M, Sg, gdg, row, sm, counts);
+  }
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(128) k_count_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
+__global__ void __launch_bounds__(128, 4) k_count_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
                                                      long long n, long long* __restrict__ counts) {
   count_block<DIM>(S, M, Sg, gdg, n, (long long)blockIdx.x * blockDim.x, counts);
 }
 
-// One block of 128 consecutive rows starting at row0 (fill phase).
+// One block of 128 consecutive rows starting at row0 (fill phase): each
+// warp writes its 32 rows one at a time.
 template <int DIM>
 __device__ __forceinline__ void fill_block(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
                                            long long n, long long row0, const long long* __restrict__ row_ptr,
                                            const float* __restrict__ x, int* __restrict__ col,
                                            float* __restrict__ val, float* __restrict__ b) {
-  long long i = row0 + threadIdx.x;
-  int key = (i < n) ? nv_key(M.rdf[i].nv) : -1;
-  long long row = regroup_rows(i, key);
-  const bool live = row >= 0;
-  const RowDF& r = M.rdf[live ? row : 0];
-  __shared__ int colb[4][kChunk * kRingPitch];
-  __shared__ float valb[4][kChunk * kRingPitch];
-  const int wid = threadIdx.x >> 5;
-  FillSinkR fs;
-  fs.colb = colb[wid];
-  fs.valb = valb[wid];
-  fs.n = 0;
-  fs.lane = threadIdx.x & 31;
-  fs.col = col;
-  fs.val = val;
-  fs.pos = live ? row_ptr[row] : 0;
-  fs.direct = false;
-  fs.x = x;
-  fs.xpend = 0.f;
-  fs.sum = 0.f;
-  fs.comp = 0.f;
-  fs.constant = S.md.chord == PCT_CHORD_CONSTANT;
-  fs.hconst = (float)S.ph.g.h[0];
-  walk_row_df<DIM, true>(S, M, Sg, gdg, r, M.r64 + (live ? row : 0), live, fs);
-  if (live) b[row] = fs.sum * r.fac;
+  CoopSmem<DIM>& sm = coop_smem<DIM>();
+  const long long w0 = row0 + (threadIdx.x & ~31u);
+  for (int j = 0; j < 32; ++j) {
+    const long long row = w0 + j;
+    if (row >= n) break;
+    coop_fill_row<DIM>(S, M, Sg, row, sm, row_ptr, x, col, val, b);
+  }
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(128) k_fill_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
+__global__ void __launch_bounds__(128, 6) k_fill_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
                                                     long long n, const long long* __restrict__ row_ptr,
                                                     const float* __restrict__ x, int* __restrict__ col,
                                                     float* __restrict__ val, float* __restrict__ b) {
@@ -281,7 +112,7 @@ __device__ __forceinline__ int batch_find(const BatchInst* __restrict__ B, int n
 }
 
 template <bool kFill, int DIM>
-__global__ void __launch_bounds__(128) k_batch(const BatchInst* __restrict__ B, int n_inst, long long first,
+__global__ void __launch_bounds__(128, 4) k_batch(const BatchInst* __restrict__ B, int n_inst, long long first,
                                                long long last, unsigned long long* next) {
   __shared__ long long item_s;
   for (;;) {
@@ -299,12 +130,26 @@ __global__ void __launch_bounds__(128) k_batch(const BatchInst* __restrict__ B, 
   }
 }
 
+// opt in to more than 48 KB of dynamic shared memory where a kernel needs it
+template <class Kern>
+static void smem_attr(Kern k, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 int batch_blocks_per_sm(bool fill, int dim) {
   int nb = 0;
-  if (fill && dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<true, 2>, 128, 0);
-  if (fill && dim == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<true, 3>, 128, 0);
-  if (!fill && dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<false, 2>, 128, 0);
-  if (!fill && dim == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<false, 3>, 128, 0);
+  if (fill && dim == 2) {
+    smem_attr(k_batch<true, 2>, coop_bytes<2, true>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<true, 2>, 128, coop_bytes<2, true>());
+  }
+  if (fill && dim == 3) {
+    smem_attr(k_batch<true, 3>, coop_bytes<3, true>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<true, 3>, 128, coop_bytes<3, true>());
+  }
+  if (!fill && dim == 2)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<false, 2>, 128, coop_bytes<2, false>());
+  if (!fill && dim == 3)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<false, 3>, 128, coop_bytes<3, false>());
   return nb > 0 ? nb : 1;
 }
 
@@ -312,10 +157,16 @@ void launch_batch(bool fill, int dim, const BatchInst* B, int n_inst, long long 
                   unsigned long long* next, int grid, cudaStream_t st) {
   cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
   if (last <= first || n_inst <= 0) return;
-  if (fill && dim == 2) k_batch<true, 2><<<grid, 128, 0, st>>>(B, n_inst, first, last, next);
-  if (fill && dim == 3) k_batch<true, 3><<<grid, 128, 0, st>>>(B, n_inst, first, last, next);
-  if (!fill && dim == 2) k_batch<false, 2><<<grid, 128, 0, st>>>(B, n_inst, first, last, next);
-  if (!fill && dim == 3) k_batch<false, 3><<<grid, 128, 0, st>>>(B, n_inst, first, last, next);
+  if (fill && dim == 2) {
+    smem_attr(k_batch<true, 2>, coop_bytes<2, true>());
+    k_batch<true, 2><<<grid, 128, coop_bytes<2, true>(), st>>>(B, n_inst, first, last, next);
+  }
+  if (fill && dim == 3) {
+    smem_attr(k_batch<true, 3>, coop_bytes<3, true>());
+    k_batch<true, 3><<<grid, 128, coop_bytes<3, true>(), st>>>(B, n_inst, first, last, next);
+  }
+  if (!fill && dim == 2) k_batch<false, 2><<<grid, 128, coop_bytes<2, false>(), st>>>(B, n_inst, first, last, next);
+  if (!fill && dim == 3) k_batch<false, 3><<<grid, 128, coop_bytes<3, false>(), st>>>(B, n_inst, first, last, next);
 }
 
 // ---------------------------------------------------------------------------
@@ -324,7 +175,6 @@ void launch_batch(bool fill, int dim, const BatchInst* B, int n_inst, long long 
 // decisions and the same FP32 lengths as the fill.
 // ---------------------------------------------------------------------------
 struct DotSinkM {
-  static constexpr bool kStaged = false;
   const float* x;
   float sum, comp;
   float xpend;
@@ -338,7 +188,6 @@ struct DotSinkM {
 };
 
 struct ScatterSinkM {
-  static constexpr bool kStaged = false;
   float* g;
   float r;
   __device__ void put(int c, float len) { atomicAdd(g + c, len * r); }
@@ -397,8 +246,14 @@ MixArgs mix_args(const SimDev& S, long long n, const void* tab, void* rec) {
   M.R = split_host(S.R);
   M.tab = (const BasisDF*)tab;
   size_t rows = (size_t)(n > 0 ? n : 1);
+  const size_t o64 = (rows * sizeof(RowDF) + 255) & ~(size_t)255;
+  const size_t olead = o64 + ((rows * sizeof(PathF64) + 255) & ~(size_t)255);
+  const size_t osegg = olead + ((2 * rows * sizeof(SegP<3>) + 255) & ~(size_t)255);
   M.rdf = (RowDF*)rec;
-  M.r64 = (PathF64*)((char*)rec + ((rows * sizeof(RowDF) + 255) & ~(size_t)255));
+  M.r64 = (PathF64*)((char*)rec + o64);
+  M.lead = (char*)rec + olead;
+  M.segg = (char*)rec + osegg;
+  M.seg_stride = seg_stride_of(S.md.model, S.md.K);
   return M;
 }
 
@@ -438,9 +293,9 @@ void launch_count_mixed(const SimDev& S, const void* tab, long long n, void* rec
   int threads = 128;
   unsigned blocks = (unsigned)((n + threads - 1) / threads);
   if (S.ph.g.dim == 2)
-    k_count_mixed<2><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n, counts);
+    k_count_mixed<2><<<blocks, threads, coop_bytes<2, false>(), st>>>(S, M, Sg, gdg, n, counts);
   else
-    k_count_mixed<3><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n, counts);
+    k_count_mixed<3><<<blocks, threads, coop_bytes<3, false>(), st>>>(S, M, Sg, gdg, n, counts);
 }
 
 void launch_fill_mixed(const SimDev& S, const void* tab, long long n, const void* rec, const long long* row_ptr,
@@ -452,10 +307,13 @@ void launch_fill_mixed(const SimDev& S, const void* tab, long long n, const void
   if (!upload_args(S, M, args, st, &Sg, &gdg)) return;
   int threads = 128;
   unsigned blocks = (unsigned)((n + threads - 1) / threads);
-  if (S.ph.g.dim == 2)
-    k_fill_mixed<2><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n, row_ptr, x, col, val, b);
-  else
-    k_fill_mixed<3><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n, row_ptr, x, col, val, b);
+  if (S.ph.g.dim == 2) {
+    smem_attr(k_fill_mixed<2>, coop_bytes<2, true>());
+    k_fill_mixed<2><<<blocks, threads, coop_bytes<2, true>(), st>>>(S, M, Sg, gdg, n, row_ptr, x, col, val, b);
+  } else {
+    smem_attr(k_fill_mixed<3>, coop_bytes<3, true>());
+    k_fill_mixed<3><<<blocks, threads, coop_bytes<3, true>(), st>>>(S, M, Sg, gdg, n, row_ptr, x, col, val, b);
+  }
 }
 
 void launch_proj_mixed(bool adjoint, const SimDev& S, const void* tab, long long row_base, long long n, void* rec,
@@ -480,9 +338,16 @@ void launch_proj_mixed(bool adjoint, const SimDev& S, const void* tab, long long
   }
 }
 
-size_t mixed_record_size(long long rows) {
+int seg_stride_of(int model, int K) {
+  const int nseg = model == PCT_PATH_SPLINE ? K + 2 : (model == PCT_PATH_STRAIGHT_MCS ? 3 : 1);
+  return nseg < 1 ? 1 : (nseg > kSegMax ? kSegMax : nseg);
+}
+
+size_t mixed_record_size(long long rows, int dim, int model, int K) {
   size_t r = (size_t)(rows > 0 ? rows : 1);
-  return ((r * sizeof(RowDF) + 255) & ~(size_t)255) + r * sizeof(PathF64) + 256;
+  const size_t seg = dim == 3 ? sizeof(SegG<3>) : sizeof(SegG<2>);
+  return ((r * sizeof(RowDF) + 255) & ~(size_t)255) + ((r * sizeof(PathF64) + 255) & ~(size_t)255) +
+         ((2 * r * sizeof(SegP<3>) + 255) & ~(size_t)255) + r * (size_t)seg_stride_of(model, K) * seg + 256;
 }
 
 }  // namespace pct

@@ -221,6 +221,7 @@ struct SegDF {
   int idx[3], kn[3], step[3];
   Ev in, out;
   df s_in, s_out;
+  unsigned inert;  // axes the segment runs along inside one slab (no crossing)
 };
 
 // Where the FP64 definition of a segment can be rebuilt: kernel arguments
@@ -291,19 +292,68 @@ __device__ __forceinline__ int cmp_ev(const GridDev& g, const GridDF& gd, const 
   return cmp_vals<DIM>(g, s, e1, ev_df<DIM>(s, gd, e1), e2, ev_df<DIM>(s, gd, e2), ends);
 }
 
+// Slab k of axis a (plane k <= X < plane k + 1, any integer k) holding X
+// at more than the margin from both planes, or false.  The margin covers
+// the double-float vertex error and the FP64 definition's rounding of a
+// plane position or of a point's floor.
+template <int DIM>
+__device__ __forceinline__ bool slab_of(const GridDev& g, const GridDF& gd, df X, int a, float eV, int& k) {
+  const float h = gd.h[a].hi;
+  const float u = floorf((X.hi - gd.of[a]) * gd.rh[a]);
+  if (!(fabsf(u) < 1e7f)) return false;
+  k = (int)u;
+  float r = df_to_f(df_sub(X, plane_df<DIM>(gd, a, k)));
+  if (r >= h) {
+    ++k;
+    r = df_to_f(df_sub(X, plane_df<DIM>(gd, a, k)));
+  } else if (r < 0.f) {
+    --k;
+    r = df_to_f(df_sub(X, plane_df<DIM>(gd, a, k)));
+  }
+  const float mr = 4.f * (eV + 16.f * kEps44 * (fabsf(X.hi) + fabsf(gd.of[a]) + (float)g.n[a] * h));
+  return r > mr && r < h - mr;
+}
+
 // Set-up.  Returns 0: the segment misses the grid; 1: ready for walk_df;
 // 2: the sign of some axis' extent cannot be certified (walk it in FP64).
-template <int DIM>
+// With kInert, an axis whose extent cannot be certified but whose two ends
+// lie inside one slab (with margin) is inert: the FP64 definition crosses
+// none of its planes there (exactly zero extent: the axis is inactive; a
+// tiny one: every plane's crossing parameter lies far outside [0, 1]) and
+// its voxel index is that slab's; the other axes decide entry and exit.
+template <int DIM, bool kInert = false>
 __device__ __forceinline__ int seg_setup_df(const GridDev& g, const GridDF& gd, const df (&P)[3], const df (&Q)[3],
                                             float mag, SegDF& s, ExactRef ends) {
   float L2 = 0.f;
   // |V~ - V| <= eV for every vertex (double-float vertex formation, FP64 rounding)
   const float eV = 64.f * kEps44 * mag;
+  s.inert = 0u;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
     df D = df_sub(Q[a], P[a]);
     float Dh = df_to_f(D);
-    if (!(fabsf(Dh) > 4.f * eV + 4.f * kEps44 * fabsf(Dh))) return 2;
+    if (!(fabsf(Dh) > 4.f * eV + 4.f * kEps44 * fabsf(Dh))) {
+      if constexpr (!kInert) {
+        return 2;
+      } else {
+        int kp, kq;
+        if (!slab_of<DIM>(g, gd, P[a], a, eV, kp) || !slab_of<DIM>(g, gd, Q[a], a, eV, kq) || kp != kq) return 2;
+        if (kp < 0 || kp > g.n[a] - 1) return 0;  // beside the grid along a
+        L2 = fmaf(Dh, Dh, L2);
+        s.inert |= 1u << a;
+        s.P[a] = P[a];
+        s.D[a] = D;
+        s.inv[a] = df{0.f, 0.f};
+        s.dl[a] = df{3e30f, 0.f};
+        s.sn[a] = df{3e30f, 0.f};
+        s.E0[a] = 0.f;
+        s.E1[a] = 0.f;
+        s.step[a] = 1;
+        s.idx[a] = kp;
+        s.kn[a] = kp + 1;
+        continue;
+      }
+    }
     L2 = fmaf(Dh, Dh, L2);
     s.P[a] = P[a];
     s.D[a] = D;
@@ -330,6 +380,7 @@ __device__ __forceinline__ int seg_setup_df(const GridDev& g, const GridDF& gd, 
   df vin{0.f, 0.f}, vout{1.f, 0.f};
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
+    if (s.inert >> a & 1u) continue;
     Ev lo{a, s.step[a] > 0 ? 0 : g.n[a]};
     Ev hi{a, s.step[a] > 0 ? g.n[a] : 0};
     df vlo = sigma_df<DIM>(s, gd, a, lo.k), vhi = sigma_df<DIM>(s, gd, a, hi.k);
@@ -349,6 +400,7 @@ __device__ __forceinline__ int seg_setup_df(const GridDev& g, const GridDF& gd, 
   const float sin_f = df_to_f(vin);
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
+    if (s.inert >> a & 1u) continue;
     const int n = g.n[a];
     int i;
     if (s.in.ax == a) {
@@ -398,6 +450,7 @@ __device__ __forceinline__ bool seg_setup_fast(const GridDev& g, const GridDF& g
                                                float mag, SegDF& s, Walk32& w) {
   const float eV = 64.f * kEps44 * mag;
   float L2 = 0.f;
+  s.inert = 0u;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
     const float lo = gd.of[a], span = (float)g.n[a] * gd.h[a].hi, m = 1e-3f * gd.h[a].hi;
@@ -616,6 +669,9 @@ struct MixArgs {
   const BasisDF* tab;   // [K + 1]
   RowDF* rdf;           // [rows]
   PathF64* r64;         // [rows]
+  void* lead;           // [rows][2] summaries of the lead-in / lead-out segments
+  void* segg;           // [rows][seg_stride] compact segment records (count -> fill)
+  int seg_stride;
 };
 
 // one simulation of a batch (a global-memory copy of its arguments and its
