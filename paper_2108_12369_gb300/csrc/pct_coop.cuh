@@ -181,14 +181,14 @@ __device__ __forceinline__ SegP<DIM>* lead_rec(const MixArgs& M, long long row) 
 // Compact segment record.  The count kernel writes one per segment (row
 // stride: the model's largest segment count); the fill reads them instead
 // of setting the segments up again.  Words (DIM = 2 | 3):
-//   ph0[DIM] hv[DIM] cb[DIM] send L first col0 misc cnt (u16 pairs) cbase ebase
-// cbase / ebase: the segment's first crossing / entry within the row.
+//   ph0[DIM] hv[DIM] cb[DIM] send L first col0 misc cnt (u16 pairs) ebase
+// ebase: the segment's first entry within the row.
 // ---------------------------------------------------------------------------
 template <int DIM>
 struct SegW {
   static constexpr int PH0 = 0, HV = DIM, CB = 2 * DIM, SEND = 3 * DIM, L = 3 * DIM + 1, FIRST = 3 * DIM + 2,
-                       COL0 = 3 * DIM + 3, MISC = 3 * DIM + 4, CNT = 3 * DIM + 5, CBASE = CNT + (DIM + 1) / 2,
-                       EBASE = CBASE + 1, NV = (EBASE + 4) / 4;  // int4 per record
+                       COL0 = 3 * DIM + 3, MISC = 3 * DIM + 4, CNT = 3 * DIM + 5, EBASE = CNT + (DIM + 1) / 2,
+                       NV = (EBASE + 4) / 4;  // int4 per record
 };
 
 template <int DIM>
@@ -262,7 +262,8 @@ struct CoopSmem {
   SegG<DIM> tab[kSegMax];
   unsigned bits[kRowCross / 32 + 4];  // segment starts among the row's crossings
   unsigned char ord[kSegMax];         // k-th segment with crossings
-  int aux[kSegMax];                   // count: first crossing of axes >= 1
+  int aux[kSegMax];                   // first position of each segment in the current pass
+  float tail[kSegMax];                // fill: merged length added to a segment's last entry
 };
 
 template <int DIM>
@@ -447,22 +448,6 @@ __device__ __forceinline__ Axes<DIM> rotate(const SegR<DIM>& R, int a, const int
   return X;
 }
 
-// axis of crossing number l of a segment (axes in order, crossings of each
-// axis consecutive) and its ordinal on that axis
-template <int DIM>
-__device__ __forceinline__ void axis_of(const SegR<DIM>& R, int lo, int l, int& a, int& i) {
-  a = lo;
-  i = l;
-#pragma unroll
-  for (int t = 0; t < DIM - 1; ++t) {
-    if (t < lo) continue;
-    const int c = R.cnt(t);
-    const bool up = a == t && i >= c;
-    i = up ? i - c : i;
-    a = up ? t + 1 : a;
-  }
-}
-
 struct Cross {
   int rank;   // position among the segment's crossings
   int colv;   // voxel entered
@@ -470,47 +455,63 @@ struct Cross {
   bool last;
 };
 
-// Crossing i of axis X.ax[0].  Common path: every decision taken from the
-// FP32 bounds; *unsure is set where they cannot decide (the caller then
-// uses cross_exact).  The next crossing is the first of: this axis' next
-// plane, every other axis' first plane after the crossing.
-template <int DIM>
-__device__ __forceinline__ Cross cross_fast(const Axes<DIM>& X, int i, int col0, float send, float& ph, bool& unsure) {
+// Crossing i of axis A (known at compile time) of the segment in R, with
+// decisions taken from the FP32 bounds; *unsure is set where they cannot
+// decide (the caller then uses cross_exact).  The next crossing is the
+// first of: this axis' next plane, every other axis' first plane after it.
+template <int DIM, int A>
+__device__ __forceinline__ Cross cross_axis(const SegR<DIM>& R, int i, const int (&dc)[DIM], float& ph, bool& unsure) {
+  using W = SegW<DIM>;
+  const float p0a = R.f(W::PH0 + A), ha = R.f(W::HV + A), ca = R.f(W::CB + A);
   Cross o;
-  ph = fmaf((float)i, X.h[0], X.p0[0]);
+  ph = fmaf((float)i, ha, p0a);
   o.rank = i;
-  o.colv = col0 + (i + 1) * X.dc[0];
-  bool has = i + 1 < X.n[0];
-  float vm = fmaf((float)(i + 1), X.h[0], X.p0[0]), cm = X.c[0];
+  o.colv = R.w[W::COL0] + (i + 1) * dc[A];
+  bool has = i + 1 < R.cnt(A);
+  float vm = fmaf((float)(i + 1), ha, p0a), cm = ca;
 #pragma unroll
-  for (int k = 1; k < DIM; ++k) {
-    const float jf = rintf(__fdividef(ph - X.p0[k], X.h[k]));
-    const float pb = fmaf(jf, X.h[k], X.p0[k]);
+  for (int c = 0; c < DIM; ++c) {
+    if (c == A) continue;
+    const float p0c = R.f(W::PH0 + c), hc = R.f(W::HV + c), cc = R.f(W::CB + c);
+    const int nc = R.cnt(c);
+    const float jf = rintf(__fdividef(ph - p0c, hc));
+    const float pb = fmaf(jf, hc, p0c);
     const float d = ph - pb;
     const int j = (int)jf;
-    // the clamp below settles candidates outside the counted planes
-    unsure = unsure || (j >= 0 && j < X.n[k] && !(fabsf(d) > fmaf(8.f * kU32, ph + fabsf(pb), X.c[0] + X.c[k])));
+    unsure = unsure || (j >= 0 && j < nc && !(fabsf(d) > fmaf(8.f * kU32, ph + fabsf(pb), ca + cc)));
     int nb = j + (d > 0.f ? 1 : 0);
-    nb = nb < 0 ? 0 : (nb > X.n[k] ? X.n[k] : nb);
+    nb = nb < 0 ? 0 : (nb > nc ? nc : nb);
     o.rank += nb;
-    o.colv += nb * X.dc[k];
-    if (nb < X.n[k]) {
-      const float v = fmaf((float)nb, X.h[k], X.p0[k]);
-      if (has) {
-        const float d2 = v - vm;
-        unsure = unsure || !(fabsf(d2) > fmaf(8.f * kU32, v + vm, X.c[k] + cm));
-        vm = d2 < 0.f ? v : vm;
-        cm = d2 < 0.f ? X.c[k] : cm;
-      } else {
-        vm = v;
-        cm = X.c[k];
-      }
-      has = true;
-    }
+    o.colv += nb * dc[c];
+    const float v = fmaf((float)nb, hc, p0c);
+    const bool hv_ = nb < nc;
+    const float d2 = v - vm;
+    unsure = unsure || (hv_ && has && !(fabsf(d2) > fmaf(8.f * kU32, v + vm, cc + cm)));
+    const bool take = hv_ && (!has || d2 < 0.f);
+    vm = take ? v : vm;
+    cm = take ? cc : cm;
+    has = has || hv_;
   }
   o.last = !has;
-  o.nv = has ? vm : send;
+  o.nv = has ? vm : R.f(W::SEND);
   return o;
+}
+
+// exact tie of crossing i of axis A with a plane of an axis below it:
+// common path from the FP32 bounds, *unsure where they cannot decide
+template <int DIM, int A>
+__device__ __forceinline__ void tie_axis(const SegR<DIM>& R, int i, bool& unsure) {
+  using W = SegW<DIM>;
+  const float p0a = R.f(W::PH0 + A), ha = R.f(W::HV + A), ca = R.f(W::CB + A);
+  const float ph = fmaf((float)i, ha, p0a);
+#pragma unroll
+  for (int c = 0; c < A; ++c) {
+    const float p0c = R.f(W::PH0 + c), hc = R.f(W::HV + c), cc = R.f(W::CB + c);
+    const float jf = rintf(__fdividef(ph - p0c, hc));
+    const float pb = fmaf(jf, hc, p0c);
+    const int j = (int)jf;
+    unsure = unsure || (j >= 0 && j < R.cnt(c) && !(fabsf(ph - pb) > fmaf(8.f * kU32, ph + fabsf(pb), ca + cc)));
+  }
 }
 
 // The same crossing with every decision exact: FP64 comparisons where the
@@ -570,21 +571,6 @@ static __device__ __noinline__ Cross cross_exact(const SimDev* Sg, const PathF64
   return o;
 }
 
-// Is crossing i of axis X.ax[0] exactly tied with a plane of an axis below
-// it?  Common path from the FP32 bounds; *unsure where they cannot decide.
-template <int DIM>
-__device__ __forceinline__ void tie_fast(const Axes<DIM>& X, int i, bool& unsure) {
-  const float ph = fmaf((float)i, X.h[0], X.p0[0]);
-#pragma unroll
-  for (int k = 1; k < DIM; ++k) {
-    if (X.ax[k] > X.ax[0]) continue;
-    const float jf = rintf(__fdividef(ph - X.p0[k], X.h[k]));
-    const float pb = fmaf(jf, X.h[k], X.p0[k]);
-    const int j = (int)jf;
-    unsure = unsure || (j >= 0 && j < X.n[k] && !(fabsf(ph - pb) > fmaf(8.f * kU32, ph + fabsf(pb), X.c[0] + X.c[k])));
-  }
-}
-
 template <int DIM>
 static __device__ __noinline__ bool tie_exact(const SimDev* Sg, const PathF64* p64, int s, Axes<DIM> X, int i,
                                               int col0, int misc) {
@@ -618,6 +604,95 @@ __device__ __forceinline__ float chain_after(const CoopSmem<DIM>& sm, int s, int
     if (ct > 0) break;
   }
   return v;
+}
+
+// Crossings of axis A of the row's segments, 32 per round: marks each
+// segment's first one and returns their number (positions are counted
+// segment after segment; sm.aux[s] = segment s's first position).
+template <int DIM, int A>
+__device__ __forceinline__ int axis_starts(CoopSmem<DIM>& sm, int nseg, int lane) {
+  using W = SegW<DIM>;
+  int n[2] = {0, 0}, base[2], t0, t1;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int s = lane + 32 * h;
+    if (s < nseg) {
+      const int w = reinterpret_cast<const int*>(&sm.tab[s])[W::CNT + (A >> 1)];
+      n[h] = (A & 1) ? (int)((unsigned)w >> 16) : (w & 0xffff);
+    }
+  }
+  base[0] = warp_excl_scan(n[0], lane, &t0);
+  base[1] = warp_excl_scan(n[1], lane, &t1) + t0;
+  __syncwarp();  // the previous pass has finished reading aux, bits and ord
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+    if (lane + 32 * h < nseg) sm.aux[lane + 32 * h] = base[h];
+  mark_starts(sm.bits, sm.ord, t0 + t1, n, base, lane);
+  return t0 + t1;
+}
+
+template <int DIM, int A>
+__device__ __forceinline__ void tie_rows(CoopSmem<DIM>& sm, int nseg, int lane, const SimDev* Sg, const PathF64* p64,
+                                         const int (&stride)[3], bool& tie) {
+  using W = SegW<DIM>;
+  const int tot = axis_starts<DIM, A>(sm, nseg, lane);
+  int ordbase = 0;
+  for (int p0 = 0; p0 < tot; p0 += 32) {
+    const int s = seg_at(sm.bits, sm.ord, p0, lane, ordbase);
+    const int p = p0 + lane;
+    if (p < tot) {
+      const SegR<DIM> R = load_seg<DIM>(sm.tab[s]);
+      const int i = p - sm.aux[s];
+      bool unsure = false;
+      tie_axis<DIM, A>(R, i, unsure);
+      if (unsure)
+        tie = tie || tie_exact<DIM>(Sg, p64, s, rotate<DIM>(R, A, stride), i, R.w[W::COL0], R.w[W::MISC]);
+    }
+  }
+}
+
+// per-row output of the fill
+struct FillOut {
+  int* col;  // the row's first CSR position
+  float* val;
+  int len;   // entries of the row
+  const float* x;
+  int nvox;
+  bool constant;
+  float hconst;
+};
+
+// every crossing of axis A: one entry each
+template <int DIM, int A>
+__device__ __forceinline__ void fill_axis(CoopSmem<DIM>& sm, int nseg, int lane, const SimDev* Sg, const PathF64* p64,
+                                          const int (&stride)[3], const FillOut& F, Kahan& wk) {
+  using W = SegW<DIM>;
+  const int tot = axis_starts<DIM, A>(sm, nseg, lane);
+  int ordbase = 0;
+  for (int p0 = 0; p0 < tot; p0 += 32) {
+    const int s = seg_at(sm.bits, sm.ord, p0, lane, ordbase);
+    const int p = p0 + lane;
+    if (p < tot) {
+      const SegR<DIM> R = load_seg<DIM>(sm.tab[s]);
+      const int misc = R.w[W::MISC];
+      const int i = p - sm.aux[s];
+      int dc[DIM];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) dc[c] = ((misc >> (4 + c)) & 1) ? -stride[c] : stride[c];
+      bool unsure = false;
+      float ph;
+      Cross cr = cross_axis<DIM, A>(R, i, dc, ph, unsure);
+      if (unsure)
+        cr = cross_exact<DIM>(Sg, p64, s, rotate<DIM>(R, A, stride), i, R.w[W::COL0], misc, R.f(W::SEND));
+      const float v = fmaf(fmaxf(cr.nv - ph, 0.f), R.f(W::L), cr.last ? sm.tail[s] : 0.f);
+      const int o = R.w[W::EBASE] + cr.rank + ((misc & kMergeBit) ? 0 : 1);
+      if (o < F.len) {
+        F.col[o] = cr.colv;
+        F.val[o] = F.constant ? F.hconst : v;
+      }
+      wk.add(v * __ldg(F.x + ((unsigned)cr.colv < (unsigned)F.nvox ? cr.colv : 0)));
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -665,7 +740,7 @@ __device__ __forceinline__ void coop_count_row(const SimDev& S, const MixArgs& M
     __syncwarp();
 
     // 2. per-segment crossings, merges, entries; prefix sums
-    int bad = 0, merge[2] = {0, 0}, Cs[2] = {0, 0}, Cen[2] = {0, 0}, Es[2] = {0, 0};
+    int bad = 0, merge[2] = {0, 0}, Cs[2] = {0, 0}, Es[2] = {0, 0};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int s = lane + 32 * h;
@@ -683,22 +758,16 @@ __device__ __forceinline__ void coop_count_row(const SimDev& S, const MixArgs& M
           }
         }
         Cs[h] = R.C();
-        Cen[h] = Cs[h] - R.cnt(0);  // the tie search enumerates crossings of axes >= 1
         Es[h] = (st == kStRegular) ? Cs[h] + 1 - m : 0;
         merge[h] = m;
         bad |= st == kStIrregular;
       }
     }
-    int t0, t1, cb[2], eb[2], ben[2];
-    cb[0] = warp_excl_scan(Cs[0], lane, &t0);
-    cb[1] = warp_excl_scan(Cs[1], lane, &t1) + t0;
-    const int totC = t0 + t1;
+    int t0, t1, eb[2];
+    const int totC = __reduce_add_sync(0xffffffffu, Cs[0] + Cs[1]);
     eb[0] = warp_excl_scan(Es[0], lane, &t0);
     eb[1] = warp_excl_scan(Es[1], lane, &t1) + t0;
     const int totE = t0 + t1;
-    ben[0] = warp_excl_scan(Cen[0], lane, &t0);
-    ben[1] = warp_excl_scan(Cen[1], lane, &t1) + t0;
-    const int totEn = t0 + t1;
     bad |= totC > kRowCross;
     irregular = __any_sync(0xffffffffu, bad) != 0;
     __syncwarp();
@@ -708,7 +777,6 @@ __device__ __forceinline__ void coop_count_row(const SimDev& S, const MixArgs& M
       if (s < nseg) {
         int* ws = reinterpret_cast<int*>(&sm.tab[s]);
         if (merge[h]) ws[W::MISC] |= kMergeBit;
-        ws[W::CBASE] = cb[h];
         ws[W::EBASE] = eb[h];
       }
     }
@@ -717,25 +785,9 @@ __device__ __forceinline__ void coop_count_row(const SimDev& S, const MixArgs& M
     // 3. exact ties between crossings of different axes (each crossing of
     // axis a >= 1 against the nearest planes of the axes below it)
     if (!irregular) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-        if (lane + 32 * h < nseg) sm.aux[lane + 32 * h] = ben[h];
       bool tie = false;
-      mark_starts(sm.bits, sm.ord, totEn, Cen, ben, lane);
-      int ordbase = 0;
-      for (int p0 = 0; p0 < totEn; p0 += 32) {
-        const int s = seg_at(sm.bits, sm.ord, p0, lane, ordbase);
-        const int p = p0 + lane;
-        if (p < totEn) {
-          const SegR<DIM> R = load_seg<DIM>(sm.tab[s]);
-          int a, i;
-          axis_of<DIM>(R, 1, p - sm.aux[s], a, i);
-          const Axes<DIM> X = rotate<DIM>(R, a, stride);
-          bool unsure = false;
-          tie_fast<DIM>(X, i, unsure);
-          if (unsure) tie = tie || tie_exact<DIM>(Sg, p64, s, X, i, R.w[W::COL0], R.w[W::MISC]);
-        }
-      }
+      tie_rows<DIM, 1>(sm, nseg, lane, Sg, p64, stride, tie);
+      if constexpr (DIM > 2) tie_rows<DIM, DIM - 1>(sm, nseg, lane, Sg, p64, stride, tie);
       irregular = __any_sync(0xffffffffu, tie) != 0;
     }
     if (!irregular) {
@@ -779,48 +831,32 @@ __device__ __forceinline__ void coop_fill_row(const SimDev& S, const MixArgs& M,
     int4* d4 = reinterpret_cast<int4*>(sm.tab);
     for (int q = lane; q < nseg * W::NV; q += 32) d4[q] = src[q];
     __syncwarp();
-    int Cs[2] = {0, 0}, cbase[2] = {0, 0};
+    int Cs[2] = {0, 0};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int s = lane + 32 * h;
       if (s < nseg) {
-        const SegR<DIM> R = load_seg<DIM>(sm.tab[s]);
-        Cs[h] = R.C();
-        cbase[h] = R.w[W::CBASE];
+        Cs[h] = load_seg<DIM>(sm.tab[s]).C();
+        // length the first entries of the following segments add to this
+        // segment's last entry when they continue its voxel
+        sm.tail[s] = chain_after<DIM>(sm, s, nseg, 0.f);
       }
     }
     const int totC = __reduce_add_sync(0xffffffffu, Cs[0] + Cs[1]);
     if (totC <= kRowCross) {
-      mark_starts(sm.bits, sm.ord, totC, Cs, cbase, lane);
       Kahan wk{0.f, 0.f};
-      const bool constant = S.md.chord == PCT_CHORD_CONSTANT;
-      const float hconst = (float)g.h[0];
+      FillOut F;
+      F.col = col + rowstart;
+      F.val = val + rowstart;
+      F.len = (int)(rowend - rowstart);
+      F.x = x;
+      F.nvox = nvox;
+      F.constant = S.md.chord == PCT_CHORD_CONSTANT;
+      F.hconst = (float)g.h[0];
       const PathF64* p64 = M.r64 + row;
-      int ordbase = 0;
-      for (int p0 = 0; p0 < totC; p0 += 32) {
-        const int s = seg_at(sm.bits, sm.ord, p0, lane, ordbase);
-        const int p = p0 + lane;
-        if (p < totC) {
-          const SegR<DIM> R = load_seg<DIM>(sm.tab[s]);
-          const int misc = R.w[W::MISC], col0 = R.w[W::COL0];
-          const float send = R.f(W::SEND);
-          int a, i;
-          axis_of<DIM>(R, 0, p - R.w[W::CBASE], a, i);
-          const Axes<DIM> X = rotate<DIM>(R, a, stride);
-          bool unsure = false;
-          float ph;
-          Cross cr = cross_fast<DIM>(X, i, col0, send, ph, unsure);
-          if (unsure) cr = cross_exact<DIM>(Sg, p64, s, X, i, col0, misc, send);
-          float v = fmaxf(cr.nv - ph, 0.f) * R.f(W::L);
-          if (cr.last) v = chain_after<DIM>(sm, s, nseg, v);
-          const long long o = rowstart + R.w[W::EBASE] + cr.rank + 1 - ((misc & kMergeBit) ? 1 : 0);
-          if (o < rowend) {
-            col[o] = cr.colv;
-            val[o] = constant ? hconst : v;
-          }
-          wk.add(v * __ldg(x + ((unsigned)cr.colv < (unsigned)nvox ? cr.colv : 0)));
-        }
-      }
+      fill_axis<DIM, 0>(sm, nseg, lane, Sg, p64, stride, F, wk);
+      fill_axis<DIM, 1>(sm, nseg, lane, Sg, p64, stride, F, wk);
+      if constexpr (DIM > 2) fill_axis<DIM, DIM - 1>(sm, nseg, lane, Sg, p64, stride, F, wk);
       // entry 0 of every segment that does not continue the previous one
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -829,13 +865,12 @@ __device__ __forceinline__ void coop_fill_row(const SimDev& S, const MixArgs& M,
           const SegR<DIM> R = load_seg<DIM>(sm.tab[s]);
           const int misc = R.w[W::MISC];
           if ((misc & 3) == kStRegular && !(misc & kMergeBit)) {
-            float v = R.f(W::FIRST);
-            if (R.C() == 0) v = chain_after<DIM>(sm, s, nseg, v);
+            const float v = R.f(W::FIRST) + (R.C() == 0 ? sm.tail[s] : 0.f);
             const int c0 = R.w[W::COL0];
-            const long long o = rowstart + R.w[W::EBASE];
-            if (o < rowend) {
-              col[o] = c0;
-              val[o] = constant ? hconst : v;
+            const int o = R.w[W::EBASE];
+            if (o < F.len) {
+              F.col[o] = c0;
+              F.val[o] = F.constant ? F.hconst : v;
             }
             wk.add(v * __ldg(x + ((unsigned)c0 < (unsigned)nvox ? c0 : 0)));
           }

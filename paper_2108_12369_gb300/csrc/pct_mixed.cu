@@ -87,7 +87,7 @@ __device__ __forceinline__ void fill_block(const SimDev& S, const MixArgs& M, co
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(128, 6) k_fill_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
+__global__ void __launch_bounds__(128, 5) k_fill_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
                                                     long long n, const long long* __restrict__ row_ptr,
                                                     const float* __restrict__ x, int* __restrict__ col,
                                                     float* __restrict__ val, float* __restrict__ b) {
