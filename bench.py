@@ -40,7 +40,7 @@ from paper_2108_12369_gb300 import workloads as W  # noqa: E402
 METRIC = "proton paths/s (CSR generation, whole job)"
 UNIT = "paths/s"
 KERNEL_FILES = {
-    "mixed": ["pct_mixed.cu", "pct_mixed.cuh", "pct_device.cuh"],
+    "mixed": ["pct_mixed.cu", "pct_mixed.cuh", "pct_coop.cuh", "pct_walk.cuh", "pct_device.cuh"],
     "f64": ["pct_f64.cu", "pct_device.cuh"],
 }
 FILL_KERNEL = {"mixed": "k_fill_mixed", "f64": "k_fill_f64"}
