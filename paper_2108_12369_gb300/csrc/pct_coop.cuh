@@ -257,13 +257,37 @@ __device__ __forceinline__ SegR<DIM> pack_seg(const SegP<DIM>& p) {
 constexpr int kSegMax = 64;     // segments of one row handled cooperatively
 constexpr int kRowCross = 4096; // crossings of one row handled cooperatively
 
+constexpr int kQueue = 32;  // crossings per pass left to the exact path
+
+// Count: the row's segment records plus the crossing enumeration
 template <int DIM>
 struct CoopSmem {
   SegG<DIM> tab[kSegMax];
   unsigned bits[kRowCross / 32 + 4];  // segment starts among the row's crossings
   unsigned char ord[kSegMax];         // k-th segment with crossings
   int aux[kSegMax];                   // first position of each segment in the current pass
-  float tail[kSegMax];                // fill: merged length added to a segment's last entry
+  int q[kQueue];                      // crossings (segment | ordinal << 8) left to the exact path
+  int qn;
+  __device__ int cnt(int s, int a) const {
+    const int w = reinterpret_cast<const int*>(&tab[s])[SegW<DIM>::CNT + (a >> 1)];
+    return (a & 1) ? (int)((unsigned)w >> 16) : (w & 0xffff);
+  }
+};
+
+// Fill: the records expanded into per-field arrays (no unpacking per crossing)
+template <int DIM>
+struct FillSmem {
+  float4 ax[DIM][kSegMax];  // per axis: ph0, hv, 1 / hv, cb
+  int4 cn[kSegMax];         // crossings per axis (x, y, z), column of the start voxel (w)
+  int4 dc[kSegMax];         // signed column step per axis (x, y, z), first entry's CSR slot + 1 (w)
+  float4 sf[kSegMax];       // send, L, merged tail of the last entry, first entry's length
+  int misc[kSegMax];
+  unsigned bits[kRowCross / 32 + 4];
+  unsigned char ord[kSegMax];
+  int aux[kSegMax];
+  int q[kQueue];
+  int qn;
+  __device__ int cnt(int s, int a) const { return a == 0 ? cn[s].x : (a == 1 ? cn[s].y : cn[s].z); }
 };
 
 template <int DIM>
@@ -455,48 +479,6 @@ struct Cross {
   bool last;
 };
 
-// Crossing i of axis A (known at compile time) of the segment in R, with
-// decisions taken from the FP32 bounds; *unsure is set where they cannot
-// decide (the caller then uses cross_exact).  The next crossing is the
-// first of: this axis' next plane, every other axis' first plane after it.
-template <int DIM, int A>
-__device__ __forceinline__ Cross cross_axis(const SegR<DIM>& R, int i, const int (&dc)[DIM], float& ph, bool& unsure) {
-  using W = SegW<DIM>;
-  const float p0a = R.f(W::PH0 + A), ha = R.f(W::HV + A), ca = R.f(W::CB + A);
-  Cross o;
-  ph = fmaf((float)i, ha, p0a);
-  o.rank = i;
-  o.colv = R.w[W::COL0] + (i + 1) * dc[A];
-  bool has = i + 1 < R.cnt(A);
-  float vm = fmaf((float)(i + 1), ha, p0a), cm = ca;
-#pragma unroll
-  for (int c = 0; c < DIM; ++c) {
-    if (c == A) continue;
-    const float p0c = R.f(W::PH0 + c), hc = R.f(W::HV + c), cc = R.f(W::CB + c);
-    const int nc = R.cnt(c);
-    const float jf = rintf(__fdividef(ph - p0c, hc));
-    const float pb = fmaf(jf, hc, p0c);
-    const float d = ph - pb;
-    const int j = (int)jf;
-    unsure = unsure || (j >= 0 && j < nc && !(fabsf(d) > fmaf(8.f * kU32, ph + fabsf(pb), ca + cc)));
-    int nb = j + (d > 0.f ? 1 : 0);
-    nb = nb < 0 ? 0 : (nb > nc ? nc : nb);
-    o.rank += nb;
-    o.colv += nb * dc[c];
-    const float v = fmaf((float)nb, hc, p0c);
-    const bool hv_ = nb < nc;
-    const float d2 = v - vm;
-    unsure = unsure || (hv_ && has && !(fabsf(d2) > fmaf(8.f * kU32, v + vm, cc + cm)));
-    const bool take = hv_ && (!has || d2 < 0.f);
-    vm = take ? v : vm;
-    cm = take ? cc : cm;
-    has = has || hv_;
-  }
-  o.last = !has;
-  o.nv = has ? vm : R.f(W::SEND);
-  return o;
-}
-
 // exact tie of crossing i of axis A with a plane of an axis below it:
 // common path from the FP32 bounds, *unsure where they cannot decide
 template <int DIM, int A>
@@ -512,6 +494,51 @@ __device__ __forceinline__ void tie_axis(const SegR<DIM>& R, int i, bool& unsure
     const int j = (int)jf;
     unsure = unsure || (j >= 0 && j < R.cnt(c) && !(fabsf(ph - pb) > fmaf(8.f * kU32, ph + fabsf(pb), ca + cc)));
   }
+}
+
+// Crossing i of axis A (known at compile time) from the fill's arrays:
+// ax[c] = (ph0, hv, 1/hv, cb), cn = (crossings per axis, start column),
+// dc = (signed column steps, -).  Decisions from the FP32 bounds; *unsure
+// where they cannot decide (the crossing then goes to cross_exact).  The
+// next crossing is the first of: this axis' next plane, every other axis'
+// first plane after the crossing.
+template <int DIM, int A>
+__device__ __forceinline__ Cross cross_x(const float4 (&ax)[DIM], const int4& cn, const int4& dc, float send, int i,
+                                         float& ph, bool& unsure) {
+  const int na = A == 0 ? cn.x : (A == 1 ? cn.y : cn.z);
+  const int da = A == 0 ? dc.x : (A == 1 ? dc.y : dc.z);
+  Cross o;
+  ph = fmaf((float)i, ax[A].y, ax[A].x);
+  o.rank = i;
+  o.colv = cn.w + (i + 1) * da;
+  bool has = i + 1 < na;
+  float vm = fmaf((float)(i + 1), ax[A].y, ax[A].x), cm = ax[A].w;
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    if (c == A) continue;
+    const int nc = c == 0 ? cn.x : (c == 1 ? cn.y : cn.z);
+    const int dcc = c == 0 ? dc.x : (c == 1 ? dc.y : dc.z);
+    const float jf = rintf((ph - ax[c].x) * ax[c].z);
+    const float pb = fmaf(jf, ax[c].y, ax[c].x);
+    const float d = ph - pb;
+    const int j = (int)jf;
+    unsure = unsure || (j >= 0 && j < nc && !(fabsf(d) > fmaf(8.f * kU32, ph + fabsf(pb), ax[A].w + ax[c].w)));
+    int nb = j + (d > 0.f ? 1 : 0);
+    nb = nb < 0 ? 0 : (nb > nc ? nc : nb);
+    o.rank += nb;
+    o.colv += nb * dcc;
+    const float v = fmaf((float)nb, ax[c].y, ax[c].x);
+    const bool hv_ = nb < nc;
+    const float d2 = v - vm;
+    unsure = unsure || (hv_ && has && !(fabsf(d2) > fmaf(8.f * kU32, v + vm, ax[c].w + cm)));
+    const bool take = hv_ && (!has || d2 < 0.f);
+    vm = take ? v : vm;
+    cm = take ? ax[c].w : cm;
+    has = has || hv_;
+  }
+  o.last = !has;
+  o.nv = has ? vm : send;
+  return o;
 }
 
 // The same crossing with every decision exact: FP64 comparisons where the
@@ -590,36 +617,16 @@ static __device__ __noinline__ bool tie_exact(const SimDev* Sg, const PathF64* p
   return tie;
 }
 
-// length added to the last entry of segment s by the first entries of the
-// segments after it that continue its voxel
-template <int DIM>
-__device__ __forceinline__ float chain_after(const CoopSmem<DIM>& sm, int s, int nseg, float v) {
-  using W = SegW<DIM>;
-  for (int t = s + 1; t < nseg; ++t) {
-    const int* wt = reinterpret_cast<const int*>(&sm.tab[t]);
-    if (!(wt[W::MISC] & kMergeBit)) break;
-    v = v + __int_as_float(wt[W::FIRST]);
-    const int c01 = wt[W::CNT];
-    const int ct = (c01 & 0xffff) + ((unsigned)c01 >> 16) + (DIM > 2 ? wt[W::CNT + 1] & 0xffff : 0);
-    if (ct > 0) break;
-  }
-  return v;
-}
-
 // Crossings of axis A of the row's segments, 32 per round: marks each
 // segment's first one and returns their number (positions are counted
 // segment after segment; sm.aux[s] = segment s's first position).
-template <int DIM, int A>
-__device__ __forceinline__ int axis_starts(CoopSmem<DIM>& sm, int nseg, int lane) {
-  using W = SegW<DIM>;
+template <int A, class SM>
+__device__ __forceinline__ int axis_starts(SM& sm, int nseg, int lane) {
   int n[2] = {0, 0}, base[2], t0, t1;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int s = lane + 32 * h;
-    if (s < nseg) {
-      const int w = reinterpret_cast<const int*>(&sm.tab[s])[W::CNT + (A >> 1)];
-      n[h] = (A & 1) ? (int)((unsigned)w >> 16) : (w & 0xffff);
-    }
+    if (s < nseg) n[h] = sm.cnt(s, A);
   }
   base[0] = warp_excl_scan(n[0], lane, &t0);
   base[1] = warp_excl_scan(n[1], lane, &t1) + t0;
@@ -633,22 +640,42 @@ __device__ __forceinline__ int axis_starts(CoopSmem<DIM>& sm, int nseg, int lane
 
 template <int DIM, int A>
 __device__ __forceinline__ void tie_rows(CoopSmem<DIM>& sm, int nseg, int lane, const SimDev* Sg, const PathF64* p64,
-                                         const int (&stride)[3], bool& tie) {
+                                         const int (&stride)[3], bool& tie, bool& overflow) {
   using W = SegW<DIM>;
-  const int tot = axis_starts<DIM, A>(sm, nseg, lane);
+  const int tot = axis_starts<A>(sm, nseg, lane);
+  if (lane == 0) sm.qn = 0;
+  __syncwarp();
   int ordbase = 0;
+  // a round's x_true load is consumed one round later, so that it overlaps
+  // the next round's work
+  float pv = 0.f, px = 0.f;
   for (int p0 = 0; p0 < tot; p0 += 32) {
     const int s = seg_at(sm.bits, sm.ord, p0, lane, ordbase);
     const int p = p0 + lane;
+    float v = 0.f, xv = 0.f;
     if (p < tot) {
       const SegR<DIM> R = load_seg<DIM>(sm.tab[s]);
       const int i = p - sm.aux[s];
       bool unsure = false;
       tie_axis<DIM, A>(R, i, unsure);
-      if (unsure)
-        tie = tie || tie_exact<DIM>(Sg, p64, s, rotate<DIM>(R, A, stride), i, R.w[W::COL0], R.w[W::MISC]);
+      if (unsure) {
+        const int k = atomicAdd(&sm.qn, 1);
+        if (k < kQueue)
+          sm.q[k] = s | (i << 8);
+        else
+          overflow = true;
+      }
     }
   }
+  __syncwarp();
+  // the crossings the FP32 bounds could not settle
+  const int nq = min(sm.qn, kQueue);
+  for (int k = lane; k < nq; k += 32) {
+    const int s = sm.q[k] & 0xff, i = sm.q[k] >> 8;
+    const SegR<DIM> R = load_seg<DIM>(sm.tab[s]);
+    tie = tie || tie_exact<DIM>(Sg, p64, s, rotate<DIM>(R, A, stride), i, R.w[W::COL0], R.w[W::MISC]);
+  }
+  __syncwarp();
 }
 
 // per-row output of the fill
@@ -662,37 +689,115 @@ struct FillOut {
   float hconst;
 };
 
-// every crossing of axis A: one entry each
+// segment s of the fill's arrays as the exact path's view (axis A first)
+template <int DIM>
+__device__ __forceinline__ Axes<DIM> fill_axes(const FillSmem<DIM>& sm, int s, int a) {
+  float p0[DIM], h[DIM], c[DIM];
+  int n[DIM], d[DIM];
+  const int4 cn = sm.cn[s], dc = sm.dc[s];
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    const float4 v = sm.ax[k][s];
+    p0[k] = v.x;
+    h[k] = v.y;
+    c[k] = v.w;
+    n[k] = k == 0 ? cn.x : (k == 1 ? cn.y : cn.z);
+    d[k] = k == 0 ? dc.x : (k == 1 ? dc.y : dc.z);
+  }
+  int order[DIM];
+  if constexpr (DIM == 2) {
+    order[0] = a;
+    order[1] = 1 - a;
+  } else {
+    order[0] = a;
+    order[1] = a == 0 ? 1 : 0;
+    order[2] = a == 2 ? 1 : 2;
+  }
+  Axes<DIM> X;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    X.p0[k] = pick<DIM>(p0, order[k]);
+    X.h[k] = pick<DIM>(h, order[k]);
+    X.c[k] = pick<DIM>(c, order[k]);
+    X.n[k] = pick<DIM>(n, order[k]);
+    X.dc[k] = pick<DIM>(d, order[k]);
+    X.ax[k] = order[k];
+  }
+  return X;
+}
+
+// one entry: write it; returns its voxel's x_true (loaded, not yet used)
+__device__ __forceinline__ float put_entry_x(const FillOut& F, int o, int c, float v) {
+  if (o < F.len) {
+    F.col[o] = c;
+    F.val[o] = F.constant ? F.hconst : v;
+  }
+  return __ldg(F.x + ((unsigned)c < (unsigned)F.nvox ? c : 0));
+}
+
+// one entry: write it and add its WEPL term
+__device__ __forceinline__ void put_entry(const FillOut& F, int o, int c, float v, Kahan& wk) {
+  if (o < F.len) {
+    F.col[o] = c;
+    F.val[o] = F.constant ? F.hconst : v;
+  }
+  wk.add(v * __ldg(F.x + ((unsigned)c < (unsigned)F.nvox ? c : 0)));
+}
+
+// every crossing of axis A: one entry each.  Crossings the FP32 bounds
+// cannot settle are queued and redone exactly after the pass (no call in
+// the loop); *overflow when the queue was full.
 template <int DIM, int A>
-__device__ __forceinline__ void fill_axis(CoopSmem<DIM>& sm, int nseg, int lane, const SimDev* Sg, const PathF64* p64,
-                                          const int (&stride)[3], const FillOut& F, Kahan& wk) {
-  using W = SegW<DIM>;
-  const int tot = axis_starts<DIM, A>(sm, nseg, lane);
+__device__ __forceinline__ void fill_axis(FillSmem<DIM>& sm, int nseg, int lane, const SimDev* Sg, const PathF64* p64,
+                                          const FillOut& F, Kahan& wk, bool& overflow) {
+  const int tot = axis_starts<A>(sm, nseg, lane);
+  if (lane == 0) sm.qn = 0;
+  __syncwarp();
   int ordbase = 0;
+  // a round's x_true load is consumed one round later, so that it overlaps
+  // the next round's work
+  float pv = 0.f, px = 0.f;
   for (int p0 = 0; p0 < tot; p0 += 32) {
     const int s = seg_at(sm.bits, sm.ord, p0, lane, ordbase);
     const int p = p0 + lane;
+    float v = 0.f, xv = 0.f;
     if (p < tot) {
-      const SegR<DIM> R = load_seg<DIM>(sm.tab[s]);
-      const int misc = R.w[W::MISC];
-      const int i = p - sm.aux[s];
-      int dc[DIM];
+      float4 ax[DIM];
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) dc[c] = ((misc >> (4 + c)) & 1) ? -stride[c] : stride[c];
+      for (int c = 0; c < DIM; ++c) ax[c] = sm.ax[c][s];
+      const int4 cn = sm.cn[s], dc = sm.dc[s];
+      const float4 sf = sm.sf[s];
+      const int i = p - sm.aux[s];
       bool unsure = false;
       float ph;
-      Cross cr = cross_axis<DIM, A>(R, i, dc, ph, unsure);
-      if (unsure)
-        cr = cross_exact<DIM>(Sg, p64, s, rotate<DIM>(R, A, stride), i, R.w[W::COL0], misc, R.f(W::SEND));
-      const float v = fmaf(fmaxf(cr.nv - ph, 0.f), R.f(W::L), cr.last ? sm.tail[s] : 0.f);
-      const int o = R.w[W::EBASE] + cr.rank + ((misc & kMergeBit) ? 0 : 1);
-      if (o < F.len) {
-        F.col[o] = cr.colv;
-        F.val[o] = F.constant ? F.hconst : v;
+      const Cross cr = cross_x<DIM, A>(ax, cn, dc, sf.x, i, ph, unsure);
+      if (!unsure) {
+        v = fmaf(fmaxf(cr.nv - ph, 0.f), sf.y, cr.last ? sf.z : 0.f);
+        xv = put_entry_x(F, dc.w + cr.rank, cr.colv, v);
+      } else {
+        const int k = atomicAdd(&sm.qn, 1);
+        if (k < kQueue)
+          sm.q[k] = s | (i << 8);
+        else
+          overflow = true;
       }
-      wk.add(v * __ldg(F.x + ((unsigned)cr.colv < (unsigned)F.nvox ? cr.colv : 0)));
     }
+    wk.add(pv * px);
+    pv = v;
+    px = xv;
   }
+  wk.add(pv * px);
+  __syncwarp();
+  const int nq = min(sm.qn, kQueue);
+  for (int k = lane; k < nq; k += 32) {
+    const int s = sm.q[k] & 0xff, i = sm.q[k] >> 8;
+    const float4 sf = sm.sf[s];
+    const float ph = fmaf((float)i, sm.ax[A][s].y, sm.ax[A][s].x);
+    const Cross cr = cross_exact<DIM>(Sg, p64, s, fill_axes<DIM>(sm, s, A), i, sm.cn[s].w, sm.misc[s], sf.x);
+    const float v = fmaf(fmaxf(cr.nv - ph, 0.f), sf.y, cr.last ? sf.z : 0.f);
+    put_entry(F, sm.dc[s].w + cr.rank, cr.colv, v, wk);
+  }
+  __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
@@ -785,10 +890,10 @@ __device__ __forceinline__ void coop_count_row(const SimDev& S, const MixArgs& M
     // 3. exact ties between crossings of different axes (each crossing of
     // axis a >= 1 against the nearest planes of the axes below it)
     if (!irregular) {
-      bool tie = false;
-      tie_rows<DIM, 1>(sm, nseg, lane, Sg, p64, stride, tie);
-      if constexpr (DIM > 2) tie_rows<DIM, DIM - 1>(sm, nseg, lane, Sg, p64, stride, tie);
-      irregular = __any_sync(0xffffffffu, tie) != 0;
+      bool tie = false, overflow = false;
+      tie_rows<DIM, 1>(sm, nseg, lane, Sg, p64, stride, tie, overflow);
+      if constexpr (DIM > 2) tie_rows<DIM, DIM - 1>(sm, nseg, lane, Sg, p64, stride, tie, overflow);
+      irregular = __any_sync(0xffffffffu, tie || overflow) != 0;
     }
     if (!irregular) {
       SegG<DIM>* dst = (SegG<DIM>*)M.segg + row * (long long)M.seg_stride;
@@ -812,7 +917,7 @@ __device__ __forceinline__ void coop_count_row(const SimDev& S, const MixArgs& M
 // ---------------------------------------------------------------------------
 template <int DIM>
 __device__ __forceinline__ void coop_fill_row(const SimDev& S, const MixArgs& M, const SimDev* Sg, long long row,
-                                              CoopSmem<DIM>& sm, const long long* __restrict__ row_ptr,
+                                              FillSmem<DIM>& sm, const long long* __restrict__ row_ptr,
                                               const float* __restrict__ x, int* __restrict__ col,
                                               float* __restrict__ val, float* __restrict__ b) {
   using W = SegW<DIM>;
@@ -826,20 +931,44 @@ __device__ __forceinline__ void coop_fill_row(const SimDev& S, const MixArgs& M,
   if (!irregular) irregular = (reinterpret_cast<const int*>(rec)[W::MISC] & kRowIrregular) != 0;
   if (!irregular) {
     const int stride[3] = {1, g.n[0], g.n[0] * (DIM > 2 ? g.n[1] : 1)};
-    const int nvox = g.n[0] * g.n[1] * (DIM > 2 ? g.n[2] : 1);
-    const int4* src = reinterpret_cast<const int4*>(rec);
-    int4* d4 = reinterpret_cast<int4*>(sm.tab);
-    for (int q = lane; q < nseg * W::NV; q += 32) d4[q] = src[q];
-    __syncwarp();
+    // 1. the row's records, expanded: one segment per lane
     int Cs[2] = {0, 0};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int s = lane + 32 * h;
       if (s < nseg) {
-        Cs[h] = load_seg<DIM>(sm.tab[s]).C();
-        // length the first entries of the following segments add to this
-        // segment's last entry when they continue its voxel
-        sm.tail[s] = chain_after<DIM>(sm, s, nseg, 0.f);
+        const SegR<DIM> R = load_seg<DIM>(rec[s]);
+        const int misc = R.w[W::MISC];
+        int n[3] = {0, 0, 0}, d[3] = {0, 0, 0};
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          const float hv = R.f(W::HV + c);
+          sm.ax[c][s] = make_float4(R.f(W::PH0 + c), hv, hv >= kFar ? 0.f : __frcp_rn(hv), R.f(W::CB + c));
+          n[c] = R.cnt(c);
+          d[c] = ((misc >> (4 + c)) & 1) ? -stride[c] : stride[c];
+        }
+        Cs[h] = n[0] + n[1] + n[2];
+        sm.cn[s] = make_int4(n[0], n[1], n[2], R.w[W::COL0]);
+        sm.dc[s] = make_int4(d[0], d[1], d[2], R.w[W::EBASE] + ((misc & kMergeBit) ? 0 : 1));
+        sm.sf[s] = make_float4(R.f(W::SEND), R.f(W::L), 0.f, R.f(W::FIRST));
+        sm.misc[s] = misc;
+      }
+    }
+    __syncwarp();
+    // length the first entries of the following segments add to a segment's
+    // last entry when they continue its voxel
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int s = lane + 32 * h;
+      if (s < nseg) {
+        float t = 0.f;
+        for (int u = s + 1; u < nseg; ++u) {
+          if (!(sm.misc[u] & kMergeBit)) break;
+          t = t + sm.sf[u].w;
+          const int4 cu = sm.cn[u];
+          if (cu.x + cu.y + cu.z > 0) break;
+        }
+        sm.sf[s].z = t;
       }
     }
     const int totC = __reduce_add_sync(0xffffffffu, Cs[0] + Cs[1]);
@@ -850,42 +979,40 @@ __device__ __forceinline__ void coop_fill_row(const SimDev& S, const MixArgs& M,
       F.val = val + rowstart;
       F.len = (int)(rowend - rowstart);
       F.x = x;
-      F.nvox = nvox;
+      F.nvox = g.n[0] * g.n[1] * (DIM > 2 ? g.n[2] : 1);
       F.constant = S.md.chord == PCT_CHORD_CONSTANT;
       F.hconst = (float)g.h[0];
       const PathF64* p64 = M.r64 + row;
-      fill_axis<DIM, 0>(sm, nseg, lane, Sg, p64, stride, F, wk);
-      fill_axis<DIM, 1>(sm, nseg, lane, Sg, p64, stride, F, wk);
-      if constexpr (DIM > 2) fill_axis<DIM, DIM - 1>(sm, nseg, lane, Sg, p64, stride, F, wk);
-      // entry 0 of every segment that does not continue the previous one
+      bool overflow = false;
+      fill_axis<DIM, 0>(sm, nseg, lane, Sg, p64, F, wk, overflow);
+      fill_axis<DIM, 1>(sm, nseg, lane, Sg, p64, F, wk, overflow);
+      if constexpr (DIM > 2) fill_axis<DIM, DIM - 1>(sm, nseg, lane, Sg, p64, F, wk, overflow);
+      // 2. entry 0 of every segment that does not continue the previous one
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int s = lane + 32 * h;
         if (s < nseg) {
-          const SegR<DIM> R = load_seg<DIM>(sm.tab[s]);
-          const int misc = R.w[W::MISC];
+          const int misc = sm.misc[s];
           if ((misc & 3) == kStRegular && !(misc & kMergeBit)) {
-            const float v = R.f(W::FIRST) + (R.C() == 0 ? sm.tail[s] : 0.f);
-            const int c0 = R.w[W::COL0];
-            const int o = R.w[W::EBASE];
-            if (o < F.len) {
-              F.col[o] = c0;
-              F.val[o] = F.constant ? F.hconst : v;
-            }
-            wk.add(v * __ldg(x + ((unsigned)c0 < (unsigned)nvox ? c0 : 0)));
+            const int4 cn = sm.cn[s];
+            const float4 sf = sm.sf[s];
+            const float v = sf.w + (cn.x + cn.y + cn.z == 0 ? sf.z : 0.f);
+            put_entry(F, sm.dc[s].w - 1, cn.w, v, wk);
           }
         }
       }
-      // the lanes' Kahan partials, summed as double-float
-      df sum = two_sum(wk.sum, -wk.comp);
+      if (!__any_sync(0xffffffffu, overflow)) {
+        // the lanes' Kahan partials, summed as double-float
+        df sum = two_sum(wk.sum, -wk.comp);
 #pragma unroll
-      for (int d = 16; d > 0; d >>= 1) {
-        df o{__shfl_xor_sync(0xffffffffu, sum.hi, d), __shfl_xor_sync(0xffffffffu, sum.lo, d)};
-        sum = df_add(sum, o);
+        for (int d = 16; d > 0; d >>= 1) {
+          df o{__shfl_xor_sync(0xffffffffu, sum.hi, d), __shfl_xor_sync(0xffffffffu, sum.lo, d)};
+          sum = df_add(sum, o);
+        }
+        if (lane == 0) b[row] = (sum.hi + sum.lo) * r.fac;
+        __syncwarp();
+        return;
       }
-      if (lane == 0) b[row] = (sum.hi + sum.lo) * r.fac;
-      __syncwarp();
-      return;
     }
   }
   walk_row_lane0<DIM, true>(Sg, M, row, nullptr, rowstart, rowend, x, col, val, b);

@@ -14,16 +14,17 @@
 namespace pct {
 
 
-template <int DIM>
-__device__ __forceinline__ CoopSmem<DIM>& coop_smem() {
+// this warp's part of the block's dynamic shared memory
+template <class SM>
+__device__ __forceinline__ SM& warp_smem() {
   extern __shared__ __align__(16) unsigned char coop_dyn[];
-  return reinterpret_cast<CoopSmem<DIM>*>(coop_dyn)[threadIdx.x >> 5];
+  return reinterpret_cast<SM*>(coop_dyn)[threadIdx.x >> 5];
 }
 
 // dynamic shared memory of a 128-thread count / fill block
 template <int DIM, bool kFill>
 constexpr size_t coop_bytes() {
-  return 4 * sizeof(CoopSmem<DIM>);
+  return kFill ? 4 * sizeof(FillSmem<DIM>) : 4 * sizeof(CoopSmem<DIM>);
 }
 
 // One block of 128 consecutive rows starting at row0 (count phase).  Thread
@@ -55,7 +56,7 @@ __device__ __forceinline__ void count_block(const SimDev& S, const MixArgs& M, c
     }
   }
   __syncwarp();  // the warp's 32 row records are complete
-  CoopSmem<DIM>& sm = coop_smem<DIM>();
+  CoopSmem<DIM>& sm = warp_smem<CoopSmem<DIM>>();
   const long long w0 = row0 + (threadIdx.x & ~31u);
   for (int j = 0; j < 32; ++j) {
     const long long row = w0 + j;
@@ -77,7 +78,7 @@ __device__ __forceinline__ void fill_block(const SimDev& S, const MixArgs& M, co
                                            long long n, long long row0, const long long* __restrict__ row_ptr,
                                            const float* __restrict__ x, int* __restrict__ col,
                                            float* __restrict__ val, float* __restrict__ b) {
-  CoopSmem<DIM>& sm = coop_smem<DIM>();
+  FillSmem<DIM>& sm = warp_smem<FillSmem<DIM>>();
   const long long w0 = row0 + (threadIdx.x & ~31u);
   for (int j = 0; j < 32; ++j) {
     const long long row = w0 + j;
@@ -87,7 +88,7 @@ __device__ __forceinline__ void fill_block(const SimDev& S, const MixArgs& M, co
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(128, 5) k_fill_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
+__global__ void __launch_bounds__(128, 7) k_fill_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
                                                     long long n, const long long* __restrict__ row_ptr,
                                                     const float* __restrict__ x, int* __restrict__ col,
                                                     float* __restrict__ val, float* __restrict__ b) {
