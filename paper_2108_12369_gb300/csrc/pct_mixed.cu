@@ -80,9 +80,17 @@ __device__ __forceinline__ void fill_block(const SimDev& S, const MixArgs& M, co
                                            float* __restrict__ val, float* __restrict__ b) {
   FillSmem<DIM>& sm = warp_smem<FillSmem<DIM>>();
   const long long w0 = row0 + (threadIdx.x & ~31u);
+  const int lane = threadIdx.x & 31;
+  const int lines = (M.seg_stride * (int)sizeof(SegG<DIM>) + 127) / 128;
   for (int j = 0; j < 32; ++j) {
     const long long row = w0 + j;
     if (row >= n) break;
+    // the next row's segment records into L2 while this row is written
+    if (j < 31 && row + 1 < n) {
+      const char* nx = (const char*)((const SegG<DIM>*)M.segg + (row + 1) * (long long)M.seg_stride);
+      if (lane < lines) asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + 128 * lane));
+      if (lane == 31) asm volatile("prefetch.global.L2 [%0];" ::"l"(M.rdf + row + 1));
+    }
     coop_fill_row<DIM>(S, M, Sg, row, sm, row_ptr, x, col, val, b);
   }
 }
