@@ -286,11 +286,12 @@ def run_ours(args):
     # end to end through the C ABI with host buffers: angle / basis tables go
     # up from host memory inside every call, the CSR + b come back to pinned
     # host memory every step
-    h_rp = torch.empty(n_rows + 1, dtype=torch.int64, pin_memory=True)
-    h_col = torch.empty(nnz, dtype=torch.int32, pin_memory=True)
-    h_val = torch.empty(nnz, dtype=torch.float32, pin_memory=True)
-    h_b = torch.empty(n_rows, dtype=torch.float32, pin_memory=True)
-    e2e_steps = max(1, min(args.steps, 3))
+    small = args.no_e2e
+    h_rp = torch.empty(1 if small else n_rows + 1, dtype=torch.int64, pin_memory=True)
+    h_col = torch.empty(1 if small else nnz, dtype=torch.int32, pin_memory=True)
+    h_val = torch.empty(1 if small else nnz, dtype=torch.float32, pin_memory=True)
+    h_b = torch.empty(1 if small else n_rows, dtype=torch.float32, pin_memory=True)
+    e2e_steps = 0 if small else max(1, min(args.steps, 3))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -307,7 +308,7 @@ def run_ours(args):
         t = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e_value = world * n_rows * e2e_steps / e2e_s
+    e2e_value = world * n_rows * e2e_steps / e2e_s if e2e_steps else None
     K = w["model"].get("spline_segments", 1)
     h2d = len(w["angles"]) * 16 + (K + 1) * 32
     d2h = (n_rows + 1) * 8 + nnz * 8 + n_rows * 4
@@ -356,6 +357,121 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _timed(fn, reps):
+    """Mean device ms of fn() over reps calls (events on the current stream)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_project(args):
+    """Projectors (Sec. II, A x = b): matrix-free y = A x and g += A^T r over
+    10M-row chunks of the 256x256x160 head workload (100M spline paths),
+    and the explicit-CSR forward / adjoint on the NEO-2 CSR."""
+    import torch
+
+    from paper_2108_12369_gb300 import build as B, pct
+    torch.cuda.set_device(0)
+    B.build()
+    prec = {"mixed": pct.PREC_MIXED, "f64": pct.PREC_F64}[args.precision]
+    peak, peak_kind = peaks()
+    out = {"metric": "projector rows/s", "unit": "rows/s", "n_gpus": 1, "precision": args.precision,
+           "data": "synthetic", "higher_is_better": True}
+    # matrix-free on the large 3D workload
+    w = W.head_3d_large()
+    ph, geo = pct.Phantom(w["phantom"]), pct.GeometryArgs(w)
+    chunk = 10_000_000
+    ws = torch.empty(pct.projector_workspace_size(ph, geo, chunk, prec), dtype=torch.uint8, device="cuda")
+    x = torch.empty(ph.nvox, dtype=torch.float32, device="cuda")
+    pct.phantom_rasterize(ph, x)
+    y = torch.empty(chunk, dtype=torch.float32, device="cuda")
+    r = torch.ones(chunk, dtype=torch.float32, device="cuda")
+    g = torch.zeros(ph.nvox, dtype=torch.float32, device="cuda")
+    k = max(1, args.steps)
+    fwd = lambda: [pct.forward(ph, geo, None, c * chunk, chunk, x, y, ws, precision=prec) for c in range(k)]
+    adj = lambda: [pct.adjoint(ph, geo, None, c * chunk, chunk, r, g, ws, precision=prec) for c in range(k)]
+    fwd()
+    adj()
+    f_ms = _timed(fwd, 1) / k
+    a_ms = _timed(adj, 1) / k
+    out["matrix_free"] = {"workload": "head_3d_large (256x256x160 voxels of 1 mm, 500 angles x 200k spline paths)",
+                          "chunk_rows": chunk, "chunks_timed": k,
+                          "forward_ms_per_chunk": f_ms, "adjoint_ms_per_chunk": a_ms,
+                          "forward_rows_per_s": chunk / (f_ms / 1e3), "adjoint_rows_per_s": chunk / (a_ms / 1e3)}
+    del ws, y, r, g
+    # explicit CSR on NEO-2
+    w2 = W.neo2_2d_spline()
+    ph2, geo2 = pct.Phantom(w2["phantom"]), pct.GeometryArgs(w2)
+    sim = pct.simulate(ph2, geo2, prec)
+    n, nnz = geo2.n_rows, sim["nnz"]
+    x2 = sim["x_true"]
+    y2 = torch.empty(n, dtype=torch.float32, device="cuda")
+    g2 = torch.zeros(ph2.nvox, dtype=torch.float32, device="cuda")
+    r2 = torch.ones(n, dtype=torch.float32, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    pct.forward(None, None, sim, 0, n, x2, y2)
+    cf, ca = [], []
+    for _ in range(k):
+        flush.zero_()
+        cf.append(_timed(lambda: pct.forward(None, None, sim, 0, n, x2, y2), 1))
+        flush.zero_()
+        ca.append(_timed(lambda: pct.adjoint(None, None, sim, 0, n, r2, g2), 1))
+    alg = 8.0 * nnz + 8.0 * (n + 1) + 4.0 * n  # col + val, row_ptr, y (x / g gathers hit L2)
+    fm, am = statistics.mean(cf), statistics.mean(ca)
+    out["csr"] = {"workload": "neo2_2d_spline CSR (3.6M rows, %d nonzeros), L2 flushed before each call" % nnz,
+                  "forward_ms": fm, "adjoint_ms": am,
+                  "roofline_forward": {"bound": "hbm", "achieved": alg / (fm / 1e3) / 1e9, "peak": peak,
+                                       "unit": "GB/s", "frac": alg / (fm / 1e3) / 1e9 / peak,
+                                       "peak_kind": peak_kind},
+                  "roofline_adjoint": {"bound": "hbm", "achieved": alg / (am / 1e3) / 1e9, "peak": peak,
+                                       "unit": "GB/s", "frac": alg / (am / 1e3) / 1e9 / peak,
+                                       "peak_kind": peak_kind}}
+    out["value"] = out["matrix_free"]["forward_rows_per_s"]
+    print(json.dumps(out), flush=True)
+
+
+def run_batch(args):
+    """Batch scheduler: the heterogeneous instance set (2D 128^2-512^2, 3D
+    64^3-160^3, straight and spline) in one persistent launch per phase,
+    replayed from CUDA graphs, with the autotuner."""
+    import torch
+
+    from paper_2108_12369_gb300 import build as B, pct
+    torch.cuda.set_device(0)
+    B.build()
+    insts = W.batch_instances(args.batch_count, max_paths=args.batch_max_paths)
+    rows = sum(len(w["angles"]) * w["paths_per_angle"] for w in insts)
+    bt = pct.Batch(insts, autotune=True)
+    for bx, ph in zip(bt.x_true, bt.phantoms):
+        pct.phantom_rasterize(ph, bx)
+    bt.count()
+    nnz = bt.nnz()
+    bt.fill(nnz)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    ts = []
+    for _ in range(args.warmup):
+        bt.count()
+        bt.fill(nnz)
+    for _ in range(args.steps):
+        flush.zero_()
+        ts.append(_timed(lambda: (bt.count(), bt.fill(nnz)), 1))
+    ms = statistics.mean(ts)
+    gm, order = bt.params()
+    print(json.dumps({"metric": "batched proton paths/s", "value": rows / (ms / 1e3), "unit": "paths/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "data": "synthetic",
+                      "config": {"instances": len(insts), "rows": rows, "nnz": int(sum(nnz)),
+                                 "max_paths_per_instance": args.batch_max_paths,
+                                 "autotuned": {"grid_mult": gm, "order": order},
+                                 "step": "count + nnz read-back + fill of every instance"}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -369,9 +485,18 @@ def main():
     ap.add_argument("--reference-rows", type=int, default=60000)
     ap.add_argument("--angles", type=int, default=0, help="override the angle count (profiling)")
     ap.add_argument("--paths-per-angle", type=int, default=0, help="override protons per angle (profiling)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host round trip (CSR larger than host RAM)")
+    ap.add_argument("--mode", choices=["csr", "project", "batch"], default="csr",
+                    help="csr: the headline CSR generation; project / batch: the projector and batch rows")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--batch-max-paths", type=int, default=1_000_000)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "project":
+        run_project(args)
+    elif args.mode == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 
