@@ -445,7 +445,7 @@ struct pct_batch {
   unsigned long long* d_next = nullptr;   // two counters (2D, 3D launches)
   long long first3 = 0, total = 0;
   int grid_mult = 1, order_mode = 0;
-  int bps[2][2] = {{1, 1}, {1, 1}};       // resident blocks per SM [fill][dim 3]
+  int bps[3][2] = {{1, 1}, {1, 1}, {1, 1}};  // resident blocks per SM [phase][dim 3]
   int sms = 1;
   cudaGraphExec_t e_count = nullptr, e_fill = nullptr;
   cudaGraph_t g_count = nullptr, g_fill = nullptr;
@@ -477,9 +477,11 @@ void batch_phase(pct_batch& b, bool fill, cudaStream_t st) {
     for (int k = 0; k < b.n; ++k)
       launch_raster(b.items[k].phantom->dev, b.items[k].x_true_dev, b.items[k].phantom->nvox, st);
   }
-  const int f = fill ? 1 : 0;
-  launch_batch(fill, 2, b.d_inst, b.n, 0, b.first3, b.d_next, b.sms * b.bps[f][0] * b.grid_mult, st);
-  launch_batch(fill, 3, b.d_inst, b.n, b.first3, b.total, b.d_next + 1, b.sms * b.bps[f][1] * b.grid_mult, st);
+  // count: the FP64 path set-up, then the cooperative count; fill: the fill
+  for (int f = fill ? 2 : 0; f <= (fill ? 2 : 1); ++f) {
+    launch_batch(f, 2, b.d_inst, b.n, 0, b.first3, b.d_next, b.sms * b.bps[f][0] * b.grid_mult, st);
+    launch_batch(f, 3, b.d_inst, b.n, b.first3, b.total, b.d_next + 1, b.sms * b.bps[f][1] * b.grid_mult, st);
+  }
   if (!fill) {
     for (int k = 0; k < b.n; ++k)
       launch_scan_rowptr((long long*)b.items[k].row_ptr_dev, b.layouts[k].rows,
@@ -580,8 +582,8 @@ extern "C" pct_status pct_batch_create(const pct_batch_item* items, int32_t n, v
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
-  for (int f = 0; f < 2; ++f)
-    for (int d = 0; d < 2; ++d) b->bps[f][d] = batch_blocks_per_sm(f == 1, d == 0 ? 2 : 3);
+  for (int f = 0; f < 3; ++f)
+    for (int d = 0; d < 2; ++d) b->bps[f][d] = batch_blocks_per_sm(f, d == 0 ? 2 : 3);
   // instance table contents (order-independent fields)
   std::vector<BatchInst> by_item(n);
   for (int k = 0; k < n; ++k) {

@@ -27,15 +27,14 @@ constexpr size_t coop_bytes() {
   return kFill ? 4 * sizeof(FillSmem<DIM>) : 4 * sizeof(CoopSmem<DIM>);
 }
 
-// One block of 128 consecutive rows starting at row0 (count phase).  Thread
+// Path phase of one block of 128 consecutive rows starting at row0: thread
 // t forms the FP64 path of row row0 + t (the definition), keeps it and its
 // double-float copy as row records and sets up the row's lead-in and
-// lead-out segments; then each warp counts its 32 rows one at a time.  The
-// arguments may live in parameter space (one launch per simulation) or in
-// global memory (the batch kernel).
+// lead-out segments.  The arguments may live in parameter space (one
+// launch per simulation) or in global memory (the batch kernel).
 template <int DIM>
-__device__ __forceinline__ void count_block(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
-                                            long long n, long long row0, long long* __restrict__ counts) {
+__device__ __forceinline__ void path_block(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
+                                           long long n, long long row0) {
   const long long i = row0 + threadIdx.x;
   if (i < n) {
     PathF64 p = path_setup(S, i);
@@ -55,7 +54,12 @@ __device__ __forceinline__ void count_block(const SimDev& S, const MixArgs& M, c
       lead[1] = seg_prepare<DIM>(S.ph.g, M.gd, Sg, gdg, Va, Vb, r.mag, ExactRef{Sg, M.r64 + i, r.nv - 2});
     }
   }
-  __syncwarp();  // the warp's 32 row records are complete
+}
+
+// Count phase of the same block: each warp counts its 32 rows one at a time.
+template <int DIM>
+__device__ __forceinline__ void rows_block(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
+                                           long long n, long long row0, long long* __restrict__ counts) {
   CoopSmem<DIM>& sm = warp_smem<CoopSmem<DIM>>();
   const long long w0 = row0 + (threadIdx.x & ~31u);
   for (int j = 0; j < 32; ++j) {
@@ -65,10 +69,19 @@ __device__ __forceinline__ void count_block(const SimDev& S, const MixArgs& M, c
   }
 }
 
+// The count of one simulation runs as two kernels: the FP64 path set-up
+// (lane per row) and the warp-cooperative count (warp per row), so that
+// each kernel's code stays small enough for the instruction caches.
 template <int DIM>
-__global__ void __launch_bounds__(128, 4) k_count_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
+__global__ void __launch_bounds__(128) k_path_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
+                                                    long long n) {
+  path_block<DIM>(S, M, Sg, gdg, n, (long long)blockIdx.x * blockDim.x);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(128, 8) k_count_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
                                                      long long n, long long* __restrict__ counts) {
-  count_block<DIM>(S, M, Sg, gdg, n, (long long)blockIdx.x * blockDim.x, counts);
+  rows_block<DIM>(S, M, Sg, gdg, n, (long long)blockIdx.x * blockDim.x, counts);
 }
 
 // One block of 128 consecutive rows starting at row0 (fill phase): each
@@ -120,9 +133,12 @@ __device__ __forceinline__ int batch_find(const BatchInst* __restrict__ B, int n
   return lo;
 }
 
-template <bool kFill, int DIM>
-__global__ void __launch_bounds__(128, 4) k_batch(const BatchInst* __restrict__ B, int n_inst, long long first,
-                                               long long last, unsigned long long* next) {
+// phases: 0 path set-up, 1 count, 2 fill (the launch bounds follow the
+// per-simulation kernels of each phase)
+template <int kPhase, int DIM>
+__global__ void __launch_bounds__(128, kPhase == 0 ? 1 : (kPhase == 1 ? 8 : 7))
+    k_batch(const BatchInst* __restrict__ B, int n_inst, long long first, long long last,
+            unsigned long long* next) {
   __shared__ long long item_s;
   for (;;) {
     __syncthreads();
@@ -132,10 +148,12 @@ __global__ void __launch_bounds__(128, 4) k_batch(const BatchInst* __restrict__ 
     if (item >= last) return;
     const BatchInst& I = B[batch_find(B, n_inst, item)];
     const long long row0 = (item - I.item0) * 128;
-    if (kFill)
+    if constexpr (kPhase == 2)
       fill_block<DIM>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, I.row_ptr, I.x, I.col, I.val, I.b);
+    else if constexpr (kPhase == 1)
+      rows_block<DIM>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, I.row_ptr_w + 1);
     else
-      count_block<DIM>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, I.row_ptr_w + 1);
+      path_block<DIM>(I.S, I.M, &I.S, &I.M.gd, I.n, row0);
   }
 }
 
@@ -145,37 +163,42 @@ static void smem_attr(Kern k, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-int batch_blocks_per_sm(bool fill, int dim) {
+template <int kPhase, int DIM>
+static size_t batch_smem() {
+  return kPhase == 0 ? 0 : coop_bytes<DIM, kPhase == 2>();
+}
+
+template <int kPhase, int DIM>
+static int blocks_per_sm() {
   int nb = 0;
-  if (fill && dim == 2) {
-    smem_attr(k_batch<true, 2>, coop_bytes<2, true>());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<true, 2>, 128, coop_bytes<2, true>());
-  }
-  if (fill && dim == 3) {
-    smem_attr(k_batch<true, 3>, coop_bytes<3, true>());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<true, 3>, 128, coop_bytes<3, true>());
-  }
-  if (!fill && dim == 2)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<false, 2>, 128, coop_bytes<2, false>());
-  if (!fill && dim == 3)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<false, 3>, 128, coop_bytes<3, false>());
+  smem_attr(k_batch<kPhase, DIM>, batch_smem<kPhase, DIM>());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<kPhase, DIM>, 128, batch_smem<kPhase, DIM>());
   return nb > 0 ? nb : 1;
 }
 
-void launch_batch(bool fill, int dim, const BatchInst* B, int n_inst, long long first, long long last,
+int batch_blocks_per_sm(int phase, int dim) {
+  if (phase == 0) return dim == 2 ? blocks_per_sm<0, 2>() : blocks_per_sm<0, 3>();
+  if (phase == 1) return dim == 2 ? blocks_per_sm<1, 2>() : blocks_per_sm<1, 3>();
+  return dim == 2 ? blocks_per_sm<2, 2>() : blocks_per_sm<2, 3>();
+}
+
+template <int kPhase, int DIM>
+static void launch_phase(const BatchInst* B, int n_inst, long long first, long long last, unsigned long long* next,
+                         int grid, cudaStream_t st) {
+  smem_attr(k_batch<kPhase, DIM>, batch_smem<kPhase, DIM>());
+  k_batch<kPhase, DIM><<<grid, 128, batch_smem<kPhase, DIM>(), st>>>(B, n_inst, first, last, next);
+}
+
+void launch_batch(int phase, int dim, const BatchInst* B, int n_inst, long long first, long long last,
                   unsigned long long* next, int grid, cudaStream_t st) {
   cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
   if (last <= first || n_inst <= 0) return;
-  if (fill && dim == 2) {
-    smem_attr(k_batch<true, 2>, coop_bytes<2, true>());
-    k_batch<true, 2><<<grid, 128, coop_bytes<2, true>(), st>>>(B, n_inst, first, last, next);
-  }
-  if (fill && dim == 3) {
-    smem_attr(k_batch<true, 3>, coop_bytes<3, true>());
-    k_batch<true, 3><<<grid, 128, coop_bytes<3, true>(), st>>>(B, n_inst, first, last, next);
-  }
-  if (!fill && dim == 2) k_batch<false, 2><<<grid, 128, coop_bytes<2, false>(), st>>>(B, n_inst, first, last, next);
-  if (!fill && dim == 3) k_batch<false, 3><<<grid, 128, coop_bytes<3, false>(), st>>>(B, n_inst, first, last, next);
+  if (phase == 0 && dim == 2) launch_phase<0, 2>(B, n_inst, first, last, next, grid, st);
+  if (phase == 0 && dim == 3) launch_phase<0, 3>(B, n_inst, first, last, next, grid, st);
+  if (phase == 1 && dim == 2) launch_phase<1, 2>(B, n_inst, first, last, next, grid, st);
+  if (phase == 1 && dim == 3) launch_phase<1, 3>(B, n_inst, first, last, next, grid, st);
+  if (phase == 2 && dim == 2) launch_phase<2, 2>(B, n_inst, first, last, next, grid, st);
+  if (phase == 2 && dim == 3) launch_phase<2, 3>(B, n_inst, first, last, next, grid, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -301,10 +324,13 @@ void launch_count_mixed(const SimDev& S, const void* tab, long long n, void* rec
   if (!upload_args(S, M, args, st, &Sg, &gdg)) return;
   int threads = 128;
   unsigned blocks = (unsigned)((n + threads - 1) / threads);
-  if (S.ph.g.dim == 2)
+  if (S.ph.g.dim == 2) {
+    k_path_mixed<2><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n);
     k_count_mixed<2><<<blocks, threads, coop_bytes<2, false>(), st>>>(S, M, Sg, gdg, n, counts);
-  else
+  } else {
+    k_path_mixed<3><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n);
     k_count_mixed<3><<<blocks, threads, coop_bytes<3, false>(), st>>>(S, M, Sg, gdg, n, counts);
+  }
 }
 
 void launch_fill_mixed(const SimDev& S, const void* tab, long long n, const void* rec, const long long* row_ptr,

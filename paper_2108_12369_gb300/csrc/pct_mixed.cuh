@@ -690,9 +690,10 @@ struct BatchInst {
 };
 
 MixArgs mix_args(const SimDev& S, long long n, const void* tab, void* rec);
-// persistent launch over the items [first, last) (all of dimension dim)
-int batch_blocks_per_sm(bool fill, int dim);
-void launch_batch(bool fill, int dim, const BatchInst* B, int n_inst, long long first, long long last,
+// persistent launch of one phase (0 path set-up, 1 count, 2 fill) over the
+// items [first, last) (all of dimension dim)
+int batch_blocks_per_sm(int phase, int dim);
+void launch_batch(int phase, int dim, const BatchInst* B, int n_inst, long long first, long long last,
                   unsigned long long* next, int grid, cudaStream_t st);
 
 }  // namespace pct
