@@ -167,3 +167,21 @@ def test_deterministic(pct):
         b = run_gpu(pct, w, prec)
         for k in ("row_ptr", "col", "val", "b"):
             assert torch.equal(a[k], b[k])
+
+
+def test_rows_beyond_cooperative_limits(pct, orc):
+    """Rows the warp-cooperative kernels hand to the per-lane walker: splines
+    of 70 pieces (72 segments, more than one warp's 64-segment table) and
+    straight rows with more than 4096 plane crossings (0.1 mm pixels on a
+    2200 x 2200 grid, near-diagonal through the centre)."""
+    w = W.neo2_2d_spline(n_angles=6, paths_per_angle=100, n=128, h=1.6)
+    w["model"] = dict(w["model"], spline_segments=70)
+    compare(run_gpu(pct, w, "mixed"), run_oracle(orc, w))
+    w = W.neo1_2d_straight(n_angles=2, paths_per_angle=50)
+    w["phantom"] = W.phantom(2, (2200, 2200), (0.1, 0.1), skin=False)
+    w["angles"] = np.array([math.pi / 4 + 0.01, 3 * math.pi / 4 - 0.013])
+    w["model"] = W.model(W.STRAIGHT, (-10.0, 10.0))
+    g = run_gpu(pct, w, "mixed")
+    ref = run_oracle(orc, w)
+    assert np.diff(ref["row_ptr"]).min() > 4096
+    compare(g, ref)
