@@ -181,14 +181,16 @@ __device__ __forceinline__ SegP<DIM>* lead_rec(const MixArgs& M, long long row) 
 // Compact segment record.  The count kernel writes one per segment (row
 // stride: the model's largest segment count); the fill reads them instead
 // of setting the segments up again.  Words (DIM = 2 | 3):
-//   ph0[DIM] hv[DIM] cb[DIM] send L first col0 misc cnt (u16 pairs) ebase
-// ebase: the segment's first entry within the row.
+//   ph0[DIM] hv[DIM] cb[DIM] send L first col0 misc cnt (u16 pairs) ebase tail
+// ebase: the segment's first entry within the row; tail: the length the
+// first entries of the following segments add to its last entry when they
+// continue its voxel (merges across polyline joints).
 // ---------------------------------------------------------------------------
 template <int DIM>
 struct SegW {
   static constexpr int PH0 = 0, HV = DIM, CB = 2 * DIM, SEND = 3 * DIM, L = 3 * DIM + 1, FIRST = 3 * DIM + 2,
                        COL0 = 3 * DIM + 3, MISC = 3 * DIM + 4, CNT = 3 * DIM + 5, EBASE = CNT + (DIM + 1) / 2,
-                       NV = (EBASE + 4) / 4;  // int4 per record
+                       TAIL = EBASE + 1, NV = (TAIL + 4) / 4;  // int4 per record
 };
 
 template <int DIM>
@@ -886,6 +888,22 @@ __device__ __forceinline__ void coop_count_row(const SimDev& S, const MixArgs& M
       }
     }
     __syncwarp();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int s = lane + 32 * h;
+      if (s < nseg) {
+        float t = 0.f;
+        for (int u = s + 1; u < nseg; ++u) {
+          const int* wu = reinterpret_cast<const int*>(&sm.tab[u]);
+          if (!(wu[W::MISC] & kMergeBit)) break;
+          t = t + __int_as_float(wu[W::FIRST]);
+          const int c01 = wu[W::CNT];
+          if ((c01 & 0xffff) + ((unsigned)c01 >> 16) + (DIM > 2 ? wu[W::CNT + 1] & 0xffff : 0) > 0) break;
+        }
+        reinterpret_cast<int*>(&sm.tab[s])[W::TAIL] = __float_as_int(t);
+      }
+    }
+    __syncwarp();
 
     // 3. exact ties between crossings of different axes (each crossing of
     // axis a >= 1 against the nearest planes of the axes below it)
@@ -950,27 +968,11 @@ __device__ __forceinline__ void coop_fill_row(const SimDev& S, const MixArgs& M,
         Cs[h] = n[0] + n[1] + n[2];
         sm.cn[s] = make_int4(n[0], n[1], n[2], R.w[W::COL0]);
         sm.dc[s] = make_int4(d[0], d[1], d[2], R.w[W::EBASE] + ((misc & kMergeBit) ? 0 : 1));
-        sm.sf[s] = make_float4(R.f(W::SEND), R.f(W::L), 0.f, R.f(W::FIRST));
+        sm.sf[s] = make_float4(R.f(W::SEND), R.f(W::L), R.f(W::TAIL), R.f(W::FIRST));
         sm.misc[s] = misc;
       }
     }
     __syncwarp();
-    // length the first entries of the following segments add to a segment's
-    // last entry when they continue its voxel
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int s = lane + 32 * h;
-      if (s < nseg) {
-        float t = 0.f;
-        for (int u = s + 1; u < nseg; ++u) {
-          if (!(sm.misc[u] & kMergeBit)) break;
-          t = t + sm.sf[u].w;
-          const int4 cu = sm.cn[u];
-          if (cu.x + cu.y + cu.z > 0) break;
-        }
-        sm.sf[s].z = t;
-      }
-    }
     const int totC = __reduce_add_sync(0xffffffffu, Cs[0] + Cs[1]);
     if (totC <= kRowCross) {
       Kahan wk{0.f, 0.f};
