@@ -264,16 +264,6 @@ __device__ __forceinline__ df sigma_df(const SegDF& s, const GridDF& gd, int a, 
   return df_mul(df_sub(plane_df<DIM>(gd, a, k), s.P[a]), s.inv[a]);
 }
 
-template <int DIM>
-__device__ __forceinline__ df ev_df(const SegDF& s, const GridDF& gd, Ev e) {
-  if (e.ax < 0) return df{(float)e.k, 0.0f};
-  df r = sigma_df<DIM>(s, gd, 0, e.k);
-#pragma unroll
-  for (int a = 1; a < DIM; ++a)
-    if (e.ax == a) r = sigma_df<DIM>(s, gd, a, e.k);
-  return r;
-}
-
 // exact sign of sigma(e1) - sigma(e2) given their double-float values
 template <int DIM>
 __device__ __forceinline__ int cmp_vals(const GridDev& g, const SegDF& s, Ev e1, df v1, Ev e2, df v2, ExactRef ends) {
@@ -285,11 +275,6 @@ __device__ __forceinline__ int cmp_vals(const GridDev& g, const SegDF& s, Ev e1,
   if (d < -m) return -1;
   if (d > m) return 1;
   return exact_cmp(ends, e1.ax, e1.k, e2.ax, e2.k);
-}
-
-template <int DIM>
-__device__ __forceinline__ int cmp_ev(const GridDev& g, const GridDF& gd, const SegDF& s, Ev e1, Ev e2, ExactRef ends) {
-  return cmp_vals<DIM>(g, s, e1, ev_df<DIM>(s, gd, e1), e2, ev_df<DIM>(s, gd, e2), ends);
 }
 
 // Slab k of axis a (plane k <= X < plane k + 1, any integer k) holding X
@@ -434,11 +419,6 @@ struct Walk32 {
 };
 
 constexpr float kU32 = 5.9604645e-8f;  // 2^-24
-
-template <int DIM>
-__device__ __forceinline__ float w_err(const Walk32& w, int a, float ph) {
-  return fmaf(8.f * kU32, fabsf(ph) + pick<DIM>(w.ph0, a) + pick<DIM>(w.hv, a), pick<DIM>(w.e0, a));
-}
 
 // Interior fast path: both endpoints inside the grid by a margin, so
 // s_in = 0 and s_out = 1 exactly; the start voxel and the first phases come
