@@ -648,13 +648,9 @@ __device__ __forceinline__ void tie_rows(CoopSmem<DIM>& sm, int nseg, int lane, 
   if (lane == 0) sm.qn = 0;
   __syncwarp();
   int ordbase = 0;
-  // a round's x_true load is consumed one round later, so that it overlaps
-  // the next round's work
-  float pv = 0.f, px = 0.f;
   for (int p0 = 0; p0 < tot; p0 += 32) {
     const int s = seg_at(sm.bits, sm.ord, p0, lane, ordbase);
     const int p = p0 + lane;
-    float v = 0.f, xv = 0.f;
     if (p < tot) {
       const SegR<DIM> R = load_seg<DIM>(sm.tab[s]);
       const int i = p - sm.aux[s];
