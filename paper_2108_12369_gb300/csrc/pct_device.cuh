@@ -95,8 +95,20 @@ __device__ __forceinline__ U4 philox4x64_10(unsigned long long c0, unsigned long
   return o;
 }
 
+// ((double)m + 0.5) * 2^-53 for m = w >> 11 < 2^53, assembled with integer
+// operations (the FP64 pipe is this kernel's bottleneck) and bit-identical
+// to that FP64 expression: for m < 2^52 the sum is exact, (2m + 1) 2^-54;
+// above, m + 0.5 is a tie between m and m + 1 and rounds to the even one.
 __device__ __forceinline__ double word_to_uniform(unsigned long long w) {
-  return ((double)(w >> 11) + 0.5) * 0x1p-53;
+  const unsigned long long m = w >> 11;
+  const bool exact = m < (1ULL << 52);
+  const unsigned long long v = exact ? 2 * m + 1 : m + (m & 1ULL);  // value = v 2^-k, 0 < v <= 2^53
+  const int k = exact ? 54 : 53;
+  const int e = 63 - __clzll((long long)v);  // v in [2^e, 2^(e + 1))
+  const unsigned long long mant = e >= 52 ? v >> (e - 52) : v << (52 - e);
+  const unsigned long long bits =
+      ((unsigned long long)(e - k + 1023) << 52) | (mant & ((1ULL << 52) - 1ULL));
+  return __longlong_as_double((long long)bits);
 }
 
 // Sequential reader of one proton's uniform stream U_0, U_1, ...

@@ -91,9 +91,9 @@ __device__ __forceinline__ df split_d(double d) {
   long long diff = (long long)mant - (long long)(top << 29);  // |diff| <= 2^28
   // scale factors 2^(e - 1046) and 2^(e - 1075) as floats
   float s_hi = __int_as_float((e - 1046 + 127) << 23);
-  float hi = (float)top * s_hi;
+  float hi = (float)(unsigned)top * s_hi;  // top <= 2^24, |diff| <= 2^28: 32-bit conversions are exact
   float lo = 0.0f;
-  if (e >= 949) lo = (float)diff * __int_as_float((e - 1075 + 127) << 23);
+  if (e >= 949) lo = (float)(int)diff * __int_as_float((e - 1075 + 127) << 23);
   if (neg) {
     hi = -hi;
     lo = -lo;
@@ -145,27 +145,29 @@ __device__ __forceinline__ void make_rowdf(const PathF64& p, double R, float fac
   r.kind = p.kind;
   r.nv = p.nv;
   r.fac = fac;
+  // mag: a scale of the vertices' coordinates for the error bounds, from the
+  // FP32 parts of the splits (no FP64 conversions)
+  const float Rf = (float)R;
   float mag = 0.f;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
     if (p.kind == 0) {
       r.P0[a] = split_d(p.A[a]);
       r.g0[a] = split_d(p.g0[a]);
-      mag = fmaxf(mag, fabsf((float)p.A[a]) + (float)R * fabsf((float)p.g0[a]));
+      mag = fmaxf(mag, fabsf(r.P0[a].hi) + Rf * fabsf(r.g0[a].hi));
     } else {
       double D = p.P1[a] - p.P0[a];
       r.P0[a] = split_d(p.P0[a]);
       r.Dl[a] = split_d(D);
       r.g0[a] = split_d(p.g0[a]);
       r.g1[a] = split_d(p.g1[a]);
+      const float p0 = fabsf(r.P0[a].hi), dl = fabsf(r.Dl[a].hi);
+      float m = fmaxf(p0 + Rf * fabsf(r.g0[a].hi), p0 + dl + Rf * fabsf(r.g1[a].hi));
       if (p.kind == 2) {
         r.u0[a] = split_d(p.m0[a] - D);
         r.u1[a] = split_d(p.m1[a] - D);
+        m = fmaxf(m, p0 + 3.f * dl + fabsf(r.u0[a].hi) + fabsf(r.u1[a].hi));  // |m0|, |m1| <= |u| + |D|
       }
-      float m = fmaxf(fabsf((float)p.P0[a]) + (float)R * fabsf((float)p.g0[a]),
-                      fabsf((float)p.P1[a]) + (float)R * fabsf((float)p.g1[a]));
-      if (p.kind == 2) m = fmaxf(m, fabsf((float)p.P0[a]) + fabsf((float)D) + fabsf((float)p.m0[a]) +
-                                        fabsf((float)p.m1[a]));
       mag = fmaxf(mag, m);
     }
   }
