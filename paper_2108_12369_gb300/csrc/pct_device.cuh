@@ -111,6 +111,23 @@ __device__ __forceinline__ double word_to_uniform(unsigned long long w) {
   return __longlong_as_double((long long)bits);
 }
 
+// 2 u - 1 for u = word_to_uniform(w), which that FP64 expression forms
+// exactly (for u < 1/2, 2u - 1 = (2m + 1 - 2^53) 2^-53, an integer of at most
+// 53 bits; for u >= 1/2, Sterbenz), assembled with integer operations.
+__device__ __forceinline__ double word_to_sym(unsigned long long w) {
+  const unsigned long long m = w >> 11;
+  const bool exact = m < (1ULL << 52);
+  // magnitude n 2^-k, negative below 1/2
+  const unsigned long long n = exact ? (1ULL << 53) - 1ULL - 2 * m : m + (m & 1ULL) - (1ULL << 52);
+  const int k = exact ? 53 : 52;
+  if (n == 0ULL) return 0.0;
+  const int e = 63 - __clzll((long long)n);  // n in [2^e, 2^(e + 1)), e <= 52
+  const unsigned long long mant = n << (52 - e);
+  const unsigned long long bits = (exact ? (1ULL << 63) : 0ULL) | ((unsigned long long)(e - k + 1023) << 52) |
+                                  (mant & ((1ULL << 52) - 1ULL));
+  return __longlong_as_double((long long)bits);
+}
+
 // Sequential reader of one proton's uniform stream U_0, U_1, ...
 struct UniformStream {
   unsigned long long row, k0, k1;
@@ -134,6 +151,20 @@ struct UniformStream {
     x = (w == 2) ? buf.w[2] : x;
     x = (w == 3) ? buf.w[3] : x;
     return word_to_uniform(x);
+  }
+  // 2 U_j - 1, the same FP64 value, without FP64 arithmetic
+  __device__ double get_sym(long long j) {
+    long long b = j >> 2;
+    if (b != block) {
+      buf = philox4x64_10(row, (unsigned long long)b, 0ULL, 0ULL, k0, k1);
+      block = b;
+    }
+    const int w = (int)(j & 3);
+    unsigned long long x = buf.w[0];
+    x = (w == 1) ? buf.w[1] : x;
+    x = (w == 2) ? buf.w[2] : x;
+    x = (w == 3) ? buf.w[3] : x;
+    return word_to_sym(x);
   }
 };
 
@@ -167,10 +198,8 @@ __device__ __forceinline__ void normal_pair(UniformStream& us, long long& j, dou
   z1 = 0.0;
   z2 = 0.0;
   for (int attempt = 0; attempt < 64; ++attempt) {
-    double u1 = us.get(j), u2 = us.get(j + 1);
+    const double v1 = us.get_sym(j), v2 = us.get_sym(j + 1);  // 2 U - 1
     j += 2;
-    double v1 = 2.0 * u1 - 1.0;
-    double v2 = 2.0 * u2 - 1.0;
     double s = v1 * v1 + v2 * v2;
     if (s > 0.0 && s < 1.0) {
       double f = sqrt((-2.0 * own_log(s)) / s);
