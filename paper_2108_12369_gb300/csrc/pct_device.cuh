@@ -172,13 +172,17 @@ struct UniformStream {
 // Natural logarithm (atanh series after argument reduction; Cody-Waite
 // split of ln 2).  Same operations, in the same order, as the definition.
 // ---------------------------------------------------------------------------
+// Its argument is positive and normal (s of the polar method): frexp and the
+// exact doubling are done on the bits (same values, no FP64 instructions).
 __device__ __forceinline__ double own_log(double x) {
-  int e;
-  double f = frexp(x, &e);
-  if (f < 0.70710678118654752440) {
-    f = f * 2.0;
+  const unsigned long long xb = (unsigned long long)__double_as_longlong(x);
+  int e = (int)((xb >> 52) & 0x7ffULL) - 1022;                       // x = f 2^e, f in [1/2, 1)
+  unsigned long long fb = (xb & 0x800fffffffffffffULL) | (1022ULL << 52);
+  if (fb < 0x3fe6a09e667f3bcdULL) {  // f < 0.70710678118654752440 (positive doubles order as integers)
+    fb += 1ULL << 52;                 // f * 2
     e = e - 1;
   }
+  const double f = __longlong_as_double((long long)fb);
   double u = f - 1.0;
   double y = u / (f + 1.0);
   double y2 = y * y;
