@@ -31,7 +31,10 @@ __global__ void k_csr_adjoint(const long long* __restrict__ row_ptr, const int* 
   if (ri == 0.0f) return;
   long long rr = row0 + w;
   long long beg = row_ptr[rr], end = row_ptr[rr + 1];
-  for (long long e = beg + lane; e < end; e += 32) atomicAdd(g + __ldg(col + e), __ldg(val + e) * ri);
+  // plain `red` with no memory clobber (nothing here reads g): the next
+  // entries' col / val loads may be issued ahead of it
+  for (long long e = beg + lane; e < end; e += 32)
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(g + __ldg(col + e)), "f"(__ldg(val + e) * ri));
 }
 
 void launch_csr_forward(const long long* row_ptr, const int* col, const float* val, long long row0,

@@ -161,7 +161,10 @@ __global__ void k_mf_forward_f64(SimDev S, long long row0, long long n, const fl
 struct ScatterSinkF64 {
   float* g;
   float r;
-  __device__ void put(int c, double len) { atomicAdd(g + c, (float)len * r); }
+  // plain `red` with no memory clobber (nothing in the kernel reads g)
+  __device__ void put(int c, double len) {
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(g + c), "f"((float)len * r));
+  }
   __device__ void pend(int) {}
 };
 

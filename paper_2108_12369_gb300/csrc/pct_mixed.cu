@@ -56,17 +56,26 @@ __device__ __forceinline__ void path_block(const SimDev& S, const MixArgs& M, co
   }
 }
 
-// Count phase of the same block: each warp counts its 32 rows one at a time.
+// The block's 128 rows are handed out one at a time to whichever warp is
+// free (rows differ in length; a static split leaves warps idle while the
+// block's slowest warp finishes).  All 128 threads call; the counter starts
+// at `first`, the rows the warps took before the call (one each).
+__device__ __forceinline__ int next_row_of_block(int* take) {
+  int k = 0;
+  if ((threadIdx.x & 31) == 0) k = atomicAdd(take, 1);
+  return __shfl_sync(0xffffffffu, k, 0);
+}
+
+// Count phase of the same block: each warp counts one row at a time.
 template <int DIM>
 __device__ __forceinline__ void rows_block(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
                                            long long n, long long row0, long long* __restrict__ counts) {
   CoopSmem<DIM>& sm = warp_smem<CoopSmem<DIM>>();
-  const long long w0 = row0 + (threadIdx.x & ~31u);
-  for (int j = 0; j < 32; ++j) {
-    const long long row = w0 + j;
-    if (row >= n) break;
-    coop_count_row<DIM>(S, M, Sg, gdg, row, sm, counts);
-  }
+  __shared__ int take;
+  if (threadIdx.x == 0) take = 4;
+  __syncthreads();
+  for (int k = threadIdx.x >> 5; k < 128 && row0 + k < n; k = next_row_of_block(&take))
+    coop_count_row<DIM>(S, M, Sg, gdg, row0 + k, sm, counts);
 }
 
 // The count of one simulation runs as two kernels: the FP64 path set-up
@@ -85,26 +94,31 @@ __global__ void __launch_bounds__(128, 8) k_count_mixed(SimDev S, MixArgs M, con
 }
 
 // One block of 128 consecutive rows starting at row0 (fill phase): each
-// warp writes its 32 rows one at a time.
+// warp writes one row at a time.
 template <int DIM>
 __device__ __forceinline__ void fill_block(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
                                            long long n, long long row0, const long long* __restrict__ row_ptr,
                                            const float* __restrict__ x, int* __restrict__ col,
                                            float* __restrict__ val, float* __restrict__ b) {
   FillSmem<DIM>& sm = warp_smem<FillSmem<DIM>>();
-  const long long w0 = row0 + (threadIdx.x & ~31u);
   const int lane = threadIdx.x & 31;
   const int lines = (M.seg_stride * (int)sizeof(SegG<DIM>) + 127) / 128;
-  for (int j = 0; j < 32; ++j) {
-    const long long row = w0 + j;
-    if (row >= n) break;
+  __shared__ int take;
+  if (threadIdx.x == 0) take = 4;
+  __syncthreads();
+  int k = threadIdx.x >> 5;
+  while (k < 128 && row0 + k < n) {
+    const long long row = row0 + k;
+    const int kn = next_row_of_block(&take);
     // the next row's segment records into L2 while this row is written
-    if (j < 31 && row + 1 < n) {
-      const char* nx = (const char*)((const SegG<DIM>*)M.segg + (row + 1) * (long long)M.seg_stride);
+    if (kn < 128 && row0 + kn < n) {
+      const long long rn = row0 + kn;
+      const char* nx = (const char*)((const SegG<DIM>*)M.segg + rn * (long long)M.seg_stride);
       if (lane < lines) asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + 128 * lane));
-      if (lane == 31) asm volatile("prefetch.global.L2 [%0];" ::"l"(M.rdf + row + 1));
+      if (lane == 31) asm volatile("prefetch.global.L2 [%0];" ::"l"(M.rdf + rn));
     }
     coop_fill_row<DIM>(S, M, Sg, row, sm, row_ptr, x, col, val, b);
+    k = kn;
   }
 }
 
@@ -219,10 +233,16 @@ struct DotSinkM {
   }
 };
 
+// The reduction is issued as a plain `red` with no memory clobber: nothing
+// in the kernel reads g, and the compiler may then keep the row's records
+// (read from global memory) in registers across it instead of re-reading
+// them after every entry.
 struct ScatterSinkM {
   float* g;
   float r;
-  __device__ void put(int c, float len) { atomicAdd(g + c, len * r); }
+  __device__ void put(int c, float len) {
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(g + c), "f"(len * r));
+  }
   __device__ void pend(int) {}
 };
 
