@@ -178,6 +178,24 @@ pct_status pct_simulate_fill(const pct_phantom* ph, const pct_geometry* geo, int
                              const int64_t* row_ptr_dev, const float* x_true_dev,
                              int32_t* col_dev, float* val_dev, float* b_dev, void* stream);
 
+/* Phase 2 into HOST memory (Sec. II-C: the simulator's output is the
+ * system A, b), after pct_simulate_count with the same arguments and
+ * workspace.  row_ptr_host[0..n_rows] receives a copy of row_ptr_dev,
+ * col_host / val_host[0..nnz) and b_host[0..n_rows) the same values that
+ * pct_simulate_fill writes to device memory.  The rows are filled block by
+ * block into staging_dev (caller-owned device memory, 256-byte aligned, two
+ * halves; each half holds up to E = (staging_bytes / 2) / 8.25 entries and
+ * E / 16 rows), and each block's copy to the host runs on an internal
+ * stream while the next block is filled.  Host buffers should be pinned
+ * (page-locked) for the copies to overlap.  Synchronises: on return the
+ * host buffers are complete.  EINVAL if a single row has more entries than
+ * a half holds.  Caller owns every buffer. */
+pct_status pct_simulate_fill_host(const pct_phantom* ph, const pct_geometry* geo, int32_t precision,
+                                  void* workspace_dev, size_t workspace_bytes, const int64_t* row_ptr_dev,
+                                  const float* x_true_dev, void* staging_dev, size_t staging_bytes,
+                                  int64_t* row_ptr_host, int32_t* col_host, float* val_host, float* b_host,
+                                  void* stream);
+
 /* Whole simulation: rasterises x_true, counts, reads nnz back (synchronises
  * the stream once), allocates through alloc_fn and fills.  out receives
  * device buffers owned by the caller (free them with free_fn).  On failure

@@ -4,6 +4,7 @@
 // contraction so that its tables equal the definition bit for bit.
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -306,6 +307,100 @@ extern "C" pct_status pct_simulate_fill(const pct_phantom* ph, const pct_geometr
     launch_fill_mixed(S, (const char*)ws + L.basis32, L.rows, (const char*)ws + L.rec, rp, x, (int*)col, val, b,
                       (char*)ws + L.args, st);
   return cuda_check("fill launch");
+}
+
+// Phase 2 into host memory: the rows are filled block by block into two
+// device staging halves; the copy of one block to the host (on a second
+// stream) overlaps the fill of the next.
+extern "C" pct_status pct_simulate_fill_host(const pct_phantom* ph, const pct_geometry* g, int32_t precision,
+                                             void* ws, size_t ws_bytes, const int64_t* row_ptr_dev,
+                                             const float* x, void* staging, size_t staging_bytes,
+                                             int64_t* row_ptr_host, int32_t* col_host, float* val_host,
+                                             float* b_host, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  SimDev S;
+  Layout L;
+  pct_status rc = make_sim(ph, g, precision, ws, ws_bytes, st, S, L);
+  if (rc != PCT_OK) return rc;
+  if (!row_ptr_dev || !row_ptr_host) return fail(PCT_EINVAL, "pct_simulate_fill_host: NULL row pointers");
+  if (L.rows > 0 && (!x || !b_host || !staging)) return fail(PCT_EINVAL, "pct_simulate_fill_host: NULL argument");
+  if ((uintptr_t)staging % 256 != 0) return fail(PCT_EINVAL, "staging buffer must be 256-byte aligned");
+  // each half: E col entries, E val entries, E / 16 b values (E a multiple of 64)
+  const long long half = (long long)(staging_bytes / 2) & ~255LL;
+  const long long E = (long long)((double)half / 8.25) & ~63LL;
+  const long long Rb = E / 16;
+  if (cudaMemcpyAsync(row_ptr_host, row_ptr_dev, sizeof(int64_t) * (size_t)(L.rows + 1), cudaMemcpyDeviceToHost,
+                      st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return cuda_check("pct_simulate_fill_host: row pointers");
+  if (L.rows == 0) return PCT_OK;
+  if (E < 64) return fail(PCT_EINVAL, "staging buffer of %zu bytes is too small", staging_bytes);
+  const long long* rph = (const long long*)row_ptr_host;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev_fill[2] = {nullptr, nullptr}, ev_copy[2] = {nullptr, nullptr};
+  auto cleanup = [&]() {
+    if (cs) cudaStreamSynchronize(cs);
+    cudaStreamSynchronize(st);
+    for (int h = 0; h < 2; ++h) {
+      if (ev_fill[h]) cudaEventDestroy(ev_fill[h]);
+      if (ev_copy[h]) cudaEventDestroy(ev_copy[h]);
+    }
+    if (cs) cudaStreamDestroy(cs);
+  };
+  bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+  for (int h = 0; ok && h < 2; ++h)
+    ok = cudaEventCreateWithFlags(&ev_fill[h], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ev_copy[h], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cleanup();
+    return cuda_check("pct_simulate_fill_host: stream / events");
+  }
+  char* base = (char*)staging;
+  long long r0 = 0;
+  for (int k = 0; ok && r0 < L.rows; ++k) {
+    const long long nz0 = rph[r0];
+    // the longest block from r0 whose entries and rows fit one half
+    long long r1 = (long long)(std::upper_bound(rph + r0, rph + L.rows + 1, nz0 + E) - rph) - 1;
+    r1 = std::min(std::min(r1, r0 + Rb), (long long)L.rows);
+    if (r1 <= r0) {
+      cleanup();
+      return fail(PCT_EINVAL, "staging buffer of %zu bytes cannot hold row %lld (%lld entries)", staging_bytes,
+                  r0, rph[r0 + 1] - nz0);
+    }
+    const long long nz1 = rph[r1];
+    const int h = k & 1;
+    int* col_s = (int*)(base + h * half);
+    float* val_s = (float*)(base + h * half + 4 * E);
+    float* b_s = (float*)(base + h * half + 8 * E);
+    if (k >= 2) ok = cudaStreamWaitEvent(st, ev_copy[h], 0) == cudaSuccess;
+    if (precision == PCT_PREC_F64)  // col / val by CSR position: bases moved back by nz0 (host arithmetic)
+      launch_fill_f64(S, r0, r1 - r0, (const long long*)row_ptr_dev + r0, x,
+                      (int*)((uintptr_t)col_s - sizeof(int) * (uintptr_t)nz0),
+                      (float*)((uintptr_t)val_s - sizeof(float) * (uintptr_t)nz0), b_s, st);
+    else
+      launch_fill_mixed(S, (const char*)ws + L.basis32, L.rows, (const char*)ws + L.rec,
+                        (const long long*)row_ptr_dev, x, col_s, val_s, b_s, (char*)ws + L.args, st, r0, r1, nz0,
+                        k == 0);
+    ok = ok && cudaGetLastError() == cudaSuccess && cudaEventRecord(ev_fill[h], st) == cudaSuccess &&
+         cudaStreamWaitEvent(cs, ev_fill[h], 0) == cudaSuccess;
+    if (ok && nz1 > nz0)
+      ok = cudaMemcpyAsync(col_host + nz0, col_s, 4 * (size_t)(nz1 - nz0), cudaMemcpyDeviceToHost, cs) ==
+               cudaSuccess &&
+           cudaMemcpyAsync(val_host + nz0, val_s, 4 * (size_t)(nz1 - nz0), cudaMemcpyDeviceToHost, cs) ==
+               cudaSuccess;
+    ok = ok &&
+         cudaMemcpyAsync(b_host + r0, b_s, 4 * (size_t)(r1 - r0), cudaMemcpyDeviceToHost, cs) == cudaSuccess &&
+         cudaEventRecord(ev_copy[h], cs) == cudaSuccess;
+    r0 = r1;
+  }
+  ok = ok && cudaStreamSynchronize(cs) == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
+  if (!ok) {
+    const pct_status e = cuda_check("pct_simulate_fill_host");
+    cleanup();
+    return e != PCT_OK ? e : fail(PCT_ECUDA, "pct_simulate_fill_host: a CUDA call failed");
+  }
+  cleanup();
+  return PCT_OK;
 }
 
 extern "C" pct_status pct_simulate(const pct_phantom* ph, const pct_geometry* g, int32_t precision,

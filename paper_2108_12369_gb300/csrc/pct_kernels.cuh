@@ -14,6 +14,8 @@ void launch_raster(const PhantomDev& ph, float* x, long long nvox, cudaStream_t 
 
 // all-FP64 form (pct_f64.cu)
 void launch_count_f64(const SimDev& S, long long row0, long long n, long long* counts, cudaStream_t st);
+// rows [row0, row0 + n): row_ptr and b indexed from row0 (row_ptr[0] is
+// row row0's), col / val by CSR position
 void launch_fill_f64(const SimDev& S, long long row0, long long n, const long long* row_ptr,
                      const float* x, int* col, float* val, float* b, cudaStream_t st);
 void launch_mf_forward_f64(const SimDev& S, long long row0, long long n, const float* x, float* y,
@@ -33,8 +35,13 @@ void fill_basis_df(const double* s, const double* h10, const double* h11, int n,
 // args: mixed_args_bytes() of workspace for a global copy of the arguments
 void launch_count_mixed(const SimDev& S, const void* tab, long long n, void* rec, long long* counts, void* args,
                         cudaStream_t st);
+// fill of rows [row_begin, row_end) (row_end < 0: n) of the n-row
+// simulation: entries at CSR position k go to col / val[k - nz0], row r's
+// WEPL to b[r - row_begin] (b[r] for the whole simulation).  upload = false
+// reuses the argument copy of an earlier launch with the same S.
 void launch_fill_mixed(const SimDev& S, const void* tab, long long n, const void* rec, const long long* row_ptr,
-                       const float* x, int* col, float* val, float* b, void* args, cudaStream_t st);
+                       const float* x, int* col, float* val, float* b, void* args, cudaStream_t st,
+                       long long row_begin = 0, long long row_end = -1, long long nz0 = 0, bool upload = true);
 
 // matrix-free projector, rows [row_base, row_base + n): y = A x (in = x,
 // out = y[n]) or g += A^T r (in = r[n], out = g); rec holds n rows of records

@@ -8,6 +8,8 @@
 //          per lane summed in double-float, noise factor.
 //   batch: one persistent launch of either phase over many simulations.
 //   projectors: matrix-free y = A x / g += A^T r with the per-lane walker.
+#include <cstdint>
+
 #include "pct_kernels.cuh"
 #include "pct_coop.cuh"
 
@@ -128,6 +130,18 @@ __global__ void __launch_bounds__(128, 7) k_fill_mixed(SimDev S, MixArgs M, cons
                                                     const float* __restrict__ x, int* __restrict__ col,
                                                     float* __restrict__ val, float* __restrict__ b) {
   fill_block<DIM>(S, M, Sg, gdg, n, (long long)blockIdx.x * blockDim.x, row_ptr, x, col, val, b);
+}
+
+// rows [row_begin, n) only (a kernel of its own, so that the whole fill
+// keeps its first row at compile-time zero)
+template <int DIM>
+__global__ void __launch_bounds__(128, 7) k_fill_mixed_range(SimDev S, MixArgs M, const SimDev* Sg,
+                                                          const GridDF* gdg, long long n,
+                                                          const long long* __restrict__ row_ptr,
+                                                          const float* __restrict__ x, int* __restrict__ col,
+                                                          float* __restrict__ val, float* __restrict__ b,
+                                                          long long row_begin) {
+  fill_block<DIM>(S, M, Sg, gdg, n, row_begin + (long long)blockIdx.x * blockDim.x, row_ptr, x, col, val, b);
 }
 
 // ---------------------------------------------------------------------------
@@ -325,12 +339,17 @@ size_t mixed_args_bytes() { return ((sizeof(SimDev) + 255) & ~(size_t)255) + siz
 
 // the kernel arguments, also copied to global memory for the out-of-line
 // exact comparisons (the copies are staged before cudaMemcpyAsync returns)
+static void args_at(void* args, const SimDev** Sg, const GridDF** gdg) {
+  char* base = (char*)args;
+  *Sg = (const SimDev*)base;
+  *gdg = (const GridDF*)(base + ((sizeof(SimDev) + 255) & ~(size_t)255));
+}
+
 static bool upload_args(const SimDev& S, const MixArgs& M, void* args, cudaStream_t st, const SimDev** Sg,
                         const GridDF** gdg) {
   char* base = (char*)args;
   size_t off = (sizeof(SimDev) + 255) & ~(size_t)255;
-  *Sg = (const SimDev*)base;
-  *gdg = (const GridDF*)(base + off);
+  args_at(args, Sg, gdg);
   return cudaMemcpyAsync(base, &S, sizeof(SimDev), cudaMemcpyHostToDevice, st) == cudaSuccess &&
          cudaMemcpyAsync(base + off, &M.gd, sizeof(GridDF), cudaMemcpyHostToDevice, st) == cudaSuccess;
 }
@@ -354,20 +373,46 @@ void launch_count_mixed(const SimDev& S, const void* tab, long long n, void* rec
 }
 
 void launch_fill_mixed(const SimDev& S, const void* tab, long long n, const void* rec, const long long* row_ptr,
-                       const float* x, int* col, float* val, float* b, void* args, cudaStream_t st) {
-  if (n <= 0) return;
+                       const float* x, int* col, float* val, float* b, void* args, cudaStream_t st,
+                       long long row_begin, long long row_end, long long nz0, bool upload) {
+  if (row_end < 0) row_end = n;
+  if (n <= 0 || row_end <= row_begin) return;
   MixArgs M = mix_args(S, n, tab, (void*)rec);
   const SimDev* Sg;
   const GridDF* gdg;
-  if (!upload_args(S, M, args, st, &Sg, &gdg)) return;
-  int threads = 128;
-  unsigned blocks = (unsigned)((n + threads - 1) / threads);
-  if (S.ph.g.dim == 2) {
-    smem_attr(k_fill_mixed<2>, coop_bytes<2, true>());
-    k_fill_mixed<2><<<blocks, threads, coop_bytes<2, true>(), st>>>(S, M, Sg, gdg, n, row_ptr, x, col, val, b);
+  if (upload) {
+    if (!upload_args(S, M, args, st, &Sg, &gdg)) return;
   } else {
-    smem_attr(k_fill_mixed<3>, coop_bytes<3, true>());
-    k_fill_mixed<3><<<blocks, threads, coop_bytes<3, true>(), st>>>(S, M, Sg, gdg, n, row_ptr, x, col, val, b);
+    args_at(args, &Sg, &gdg);
+  }
+  int threads = 128;
+  unsigned blocks = (unsigned)((row_end - row_begin + threads - 1) / threads);
+  const bool whole = row_begin == 0 && row_end == n && nz0 == 0;
+  // a block of rows into staging buffers: the kernels address col / val by
+  // CSR position and b by row, so the bases move back by the block's first
+  // position / row (address arithmetic on the host; every address the
+  // kernels form lies inside the staging buffers)
+  col = (int*)((uintptr_t)col - sizeof(int) * (uintptr_t)nz0);
+  val = (float*)((uintptr_t)val - sizeof(float) * (uintptr_t)nz0);
+  b = (float*)((uintptr_t)b - sizeof(float) * (uintptr_t)row_begin);
+  if (S.ph.g.dim == 2) {
+    if (whole) {
+      smem_attr(k_fill_mixed<2>, coop_bytes<2, true>());
+      k_fill_mixed<2><<<blocks, threads, coop_bytes<2, true>(), st>>>(S, M, Sg, gdg, n, row_ptr, x, col, val, b);
+    } else {
+      smem_attr(k_fill_mixed_range<2>, coop_bytes<2, true>());
+      k_fill_mixed_range<2><<<blocks, threads, coop_bytes<2, true>(), st>>>(S, M, Sg, gdg, row_end, row_ptr, x, col,
+                                                                          val, b, row_begin);
+    }
+  } else {
+    if (whole) {
+      smem_attr(k_fill_mixed<3>, coop_bytes<3, true>());
+      k_fill_mixed<3><<<blocks, threads, coop_bytes<3, true>(), st>>>(S, M, Sg, gdg, n, row_ptr, x, col, val, b);
+    } else {
+      smem_attr(k_fill_mixed_range<3>, coop_bytes<3, true>());
+      k_fill_mixed_range<3><<<blocks, threads, coop_bytes<3, true>(), st>>>(S, M, Sg, gdg, row_end, row_ptr, x, col,
+                                                                          val, b, row_begin);
+    }
   }
 }
 

@@ -65,7 +65,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 # every symbol include/pct.h declares
 EXPORTS = ["pct_phantom_create", "pct_phantom_destroy", "pct_phantom_nvox", "pct_phantom_rasterize",
-           "pct_simulate_workspace_size", "pct_simulate_count", "pct_simulate_fill", "pct_simulate",
+           "pct_simulate_workspace_size", "pct_simulate_count", "pct_simulate_fill", "pct_simulate_fill_host",
+           "pct_simulate",
            "pct_projector_workspace_size", "pct_forward", "pct_adjoint", "pct_batch_workspace_size", "pct_batch_create",
            "pct_batch_count", "pct_batch_nnz", "pct_batch_fill", "pct_batch_params", "pct_batch_destroy",
            "pct_scan_counts_static", "pct_last_error", "pct_version"]
@@ -92,6 +93,8 @@ def lib():
             "pct_simulate_count": ([vp, P(Geometry), C.c_int32, vp, C.c_size_t, vp, vp], C.c_int),
             "pct_simulate_fill": ([vp, P(Geometry), C.c_int32, vp, C.c_size_t, vp, vp, vp, vp, vp, vp],
                                   C.c_int),
+            "pct_simulate_fill_host": ([vp, P(Geometry), C.c_int32, vp, C.c_size_t, vp, vp, vp, C.c_size_t, vp, vp,
+                                        vp, vp, vp], C.c_int),
             "pct_simulate": ([vp, P(Geometry), C.c_int32, ALLOC_FN, FREE_FN, vp, P(Csr), vp], C.c_int),
             "pct_projector_workspace_size": ([vp, P(Geometry), C.c_int32, C.c_int64, P(C.c_size_t)],
                                              C.c_int),
@@ -210,6 +213,16 @@ def simulate_fill(ph, geo, precision, workspace, row_ptr, x_true, col, val, b, s
     _check(lib().pct_simulate_fill(ph.handle, C.byref(geo.c), precision, _ptr(workspace),
                                    workspace.numel() * workspace.element_size(), _ptr(row_ptr),
                                    _ptr(x_true), _ptr(col), _ptr(val), _ptr(b), _stream(stream)))
+
+
+def simulate_fill_host(ph, geo, precision, workspace, row_ptr, x_true, staging, row_ptr_h, col_h, val_h, b_h,
+                       stream=None):
+    """Phase 2 into host tensors (pinned for overlapped copies) through a
+    device staging buffer; returns when the host tensors are complete."""
+    _check(lib().pct_simulate_fill_host(ph.handle, C.byref(geo.c), precision, _ptr(workspace),
+                                        workspace.numel() * workspace.element_size(), _ptr(row_ptr),
+                                        _ptr(x_true), _ptr(staging), staging.numel() * staging.element_size(),
+                                        _ptr(row_ptr_h), _ptr(col_h), _ptr(val_h), _ptr(b_h), _stream(stream)))
 
 
 def simulate(ph: Phantom, geo: GeometryArgs, precision: int = PREC_MIXED, stream=None, device="cuda"):
