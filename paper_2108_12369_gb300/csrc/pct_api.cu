@@ -211,6 +211,8 @@ pct_status make_sim(const pct_phantom* ph, const pct_geometry* g, int precision,
   S.md.t_hi = m.t_range[1];
   S.md.v_lo = m.v_range[0];
   S.md.v_hi = m.v_range[1];
+  S.md.t_span = m.t_range[1] - m.t_range[0];
+  S.md.v_span = m.v_range[1] - m.v_range[0];
   S.md.sigma_lat = m.sigma_lat;
   S.md.sigma_in = m.sigma_in;
   S.md.sigma_out = m.sigma_out;

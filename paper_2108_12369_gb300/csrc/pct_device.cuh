@@ -40,6 +40,7 @@ struct PhantomDev {
 struct ModelDev {
   int model, chord, K, noise;
   double t_lo, t_hi, v_lo, v_hi;
+  double t_span, v_span;  // t_hi - t_lo, v_hi - v_lo (formed on the host, the same FP64 values)
   double sigma_lat, sigma_in, sigma_out, rho, rho_c;  // rho_c = sqrt(1 - rho^2)
   double noise_rel;
 };
@@ -251,18 +252,20 @@ __device__ __forceinline__ bool hull_hit(const PhantomDev& ph, const double A[3]
   return true;
 }
 
+// DIM: the grid's dimension when known at compile time (0: read from S)
+template <int DIM = 0>
 __device__ __forceinline__ PathF64 path_setup(const SimDev& S, long long row) {
   const ModelDev& md = S.md;
-  const int dim = S.ph.g.dim;
+  const int dim = DIM ? DIM : S.ph.g.dim;
   PathF64 p;
   long long k = row / S.P;
   double2 cs = S.cs[k];
   double c = cs.x, s = cs.y;
   UniformStream us;
   us.init((unsigned long long)row, S.seed, S.stream);
-  double t = md.t_lo + (md.t_hi - md.t_lo) * us.get(0);
+  double t = md.t_lo + md.t_span * us.get(0);
   double v = 0.0;
-  if (dim == 3) v = md.v_lo + (md.v_hi - md.v_lo) * us.get(1);
+  if (dim == 3) v = md.v_lo + md.v_span * us.get(1);
   long long j = 4;
   double lat_t = 0.0, ang_t = 0.0, lat_v = 0.0, ang_v = 0.0, in_t = 0.0, in_v = 0.0;
   double z1, z2;
@@ -306,10 +309,11 @@ __device__ __forceinline__ PathF64 path_setup(const SimDev& S, long long row) {
     return p;
   }
   double Q1[3], nt[3], nv3[3];
+  // in 2D the third coordinates are zero (A[2] = g0[2] = 0): not formed
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    p.P0[a] = p.A[a] + lam_in * p.g0[a];
-    Q1[a] = p.A[a] + lam_out * p.g0[a];
+    p.P0[a] = a < dim ? p.A[a] + lam_in * p.g0[a] : 0.0;
+    Q1[a] = a < dim ? p.A[a] + lam_out * p.g0[a] : 0.0;
   }
   nt[0] = -p.g0[1];
   nt[1] = p.g0[0];
@@ -339,8 +343,8 @@ __device__ __forceinline__ PathF64 path_setup(const SimDev& S, long long row) {
       if (a < dim) l = l + (p.P1[a] - p.P0[a]) * p.g0[a];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      p.m0[a] = l * p.g0[a];
-      p.m1[a] = l * p.g1[a];
+      p.m0[a] = a < dim ? l * p.g0[a] : 0.0;
+      p.m1[a] = a < dim ? l * p.g1[a] : 0.0;
     }
     p.kind = 2;
     p.nv = md.K + 3;

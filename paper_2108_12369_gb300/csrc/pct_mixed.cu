@@ -39,7 +39,7 @@ __device__ __forceinline__ void path_block(const SimDev& S, const MixArgs& M, co
                                            long long n, long long row0) {
   const long long i = row0 + threadIdx.x;
   if (i < n) {
-    PathF64 p = path_setup(S, i);
+    PathF64 p = path_setup<DIM>(S, i);
     M.r64[i] = p;  // exact decisions read the FP64 path back from here
     float fac = (S.md.noise == PCT_NOISE_GAUSS_REL) ? (float)(1.0 + S.md.noise_rel * p.z_noise) : 1.0f;
     RowDF r;
@@ -267,7 +267,7 @@ __device__ __forceinline__ void proj_block(const SimDev& S, const MixArgs& M, co
   long long i = row0 + threadIdx.x;
   int key = -1;
   if (i < n && (!kAdjoint || in[i] != 0.0f)) {
-    PathF64 p = path_setup(S, row_base + i);
+    PathF64 p = path_setup<DIM>(S, row_base + i);
     M.r64[i] = p;
     RowDF r;
     make_rowdf<DIM>(p, S.R, 1.0f, r);
