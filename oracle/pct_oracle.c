@@ -7,7 +7,8 @@
  * Build: gcc -O2 -ffp-contract=off -fopenmp -fPIC -shared pct_oracle.c -lm
  * (-ffp-contract=off matters: GCC fuses a*b+c by default on aarch64).
  *
- * Readings of the paper that this file fixes (each listed in the design doc):
+ * Readings of the paper that this file fixes (where the paper is silent or
+ * ambiguous):
  *  - regions are painted in order, later regions overwrite earlier ones;
  *    region 0 is the phantom's outer boundary (the "hull");
  *  - rand() is replaced by the counter-based Philox4x64-10 generator of
