@@ -46,7 +46,7 @@ typedef enum {
   PCT_ENOMEM = 2,       /* the caller's allocator returned NULL / workspace too small */
   PCT_ECUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
   PCT_ETIMEOUT = 4,     /* a device-side bounded wait ran out */
-  PCT_EUNSUPPORTED = 5  /* valid request this build does not implement */
+  PCT_EUNSUPPORTED = 5  /* valid request the library does not implement */
 } pct_status;
 
 enum { PCT_ELLIPSOID = 0, PCT_EXTRUDED = 1 };                /* phantom kind (3D) */
