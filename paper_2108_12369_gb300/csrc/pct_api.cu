@@ -543,6 +543,7 @@ struct pct_batch {
   long long first3 = 0, total = 0;
   int grid_mult = 1, order_mode = 0;
   int bps[3][2] = {{1, 1}, {1, 1}, {1, 1}};  // resident blocks per SM [phase][dim 3]
+  bool small[2] = {true, true};               // [dim 3]: every instance fits the smaller layout
   int sms = 1;
   cudaGraphExec_t e_count = nullptr, e_fill = nullptr;
   cudaGraph_t g_count = nullptr, g_fill = nullptr;
@@ -576,8 +577,9 @@ void batch_phase(pct_batch& b, bool fill, cudaStream_t st) {
   }
   // count: the FP64 path set-up, then the cooperative count; fill: the fill
   for (int f = fill ? 2 : 0; f <= (fill ? 2 : 1); ++f) {
-    launch_batch(f, 2, b.d_inst, b.n, 0, b.first3, b.d_next, b.sms * b.bps[f][0] * b.grid_mult, st);
-    launch_batch(f, 3, b.d_inst, b.n, b.first3, b.total, b.d_next + 1, b.sms * b.bps[f][1] * b.grid_mult, st);
+    launch_batch(f, 2, b.small[0], b.d_inst, b.n, 0, b.first3, b.d_next, b.sms * b.bps[f][0] * b.grid_mult, st);
+    launch_batch(f, 3, b.small[1], b.d_inst, b.n, b.first3, b.total, b.d_next + 1,
+                 b.sms * b.bps[f][1] * b.grid_mult, st);
   }
   if (!fill) {
     for (int k = 0; k < b.n; ++k)
@@ -679,8 +681,6 @@ extern "C" pct_status pct_batch_create(const pct_batch_item* items, int32_t n, v
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
-  for (int f = 0; f < 3; ++f)
-    for (int d = 0; d < 2; ++d) b->bps[f][d] = batch_blocks_per_sm(f, d == 0 ? 2 : 3);
   // instance table contents (order-independent fields)
   std::vector<BatchInst> by_item(n);
   for (int k = 0; k < n; ++k) {
@@ -693,7 +693,10 @@ extern "C" pct_status pct_batch_create(const pct_batch_item* items, int32_t n, v
     I.row_ptr_w = (long long*)items[k].row_ptr_dev;
     I.row_ptr = (const long long*)items[k].row_ptr_dev;
     I.x = items[k].x_true_dev;
+    if (!small_cap(I.M.seg_stride)) b->small[I.S.ph.g.dim == 3 ? 1 : 0] = false;
   }
+  for (int f = 0; f < 3; ++f)
+    for (int d = 0; d < 2; ++d) b->bps[f][d] = batch_blocks_per_sm(f, d == 0 ? 2 : 3, b->small[d]);
   auto arrange = [&]() -> pct_status {
     std::vector<BatchInst> saved = by_item;
     pct_status r = PCT_OK;

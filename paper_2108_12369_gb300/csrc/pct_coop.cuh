@@ -20,9 +20,10 @@
 // Where the FP32 bounds cannot decide, the FP64 definition does (out of
 // line).  Decisions, voxel indices, lengths and merges are those of the
 // per-lane walker.  Rows with an exact tie between crossings of different
-// axes, a segment that needs the FP64 walk, more than kSegMax segments or
-// more than kRowCross crossings are handed to the per-lane walker (lane 0
-// of the warp); the count marks them for the fill.
+// axes, a segment that needs the FP64 walk, more segments than the warp's
+// shared-memory capacity (kSegMax at most) or more than kRowCross crossings
+// are handed to the per-lane walker (lane 0 of the warp); the count marks
+// them for the fill.
 #pragma once
 #include "pct_walk.cuh"
 
@@ -256,18 +257,22 @@ __device__ __forceinline__ SegR<DIM> pack_seg(const SegP<DIM>& p) {
   return r;
 }
 
-constexpr int kSegMax = 64;     // segments of one row handled cooperatively
+constexpr int kSegMax = 64;     // segments of one row handled cooperatively (at most)
+constexpr int kSegSmall = 40;   // the smaller per-warp capacity (splines of up to 38 pieces)
 constexpr int kRowCross = 4096; // crossings of one row handled cooperatively
 
 constexpr int kQueue = 32;  // crossings per pass left to the exact path
 
-// Count: the row's segment records plus the crossing enumeration
-template <int DIM>
+// Count: the row's segment records plus the crossing enumeration, for rows
+// of up to CAP segments (a smaller CAP leaves more of the SM's on-chip
+// memory to the L1 cache)
+template <int DIM, int CAP = kSegMax>
 struct CoopSmem {
-  SegG<DIM> tab[kSegMax];
+  static constexpr int kCap = CAP;
+  SegG<DIM> tab[CAP];
   unsigned bits[kRowCross / 32 + 4];  // segment starts among the row's crossings
-  unsigned char ord[kSegMax];         // k-th segment with crossings
-  int aux[kSegMax];                   // first position of each segment in the current pass
+  unsigned char ord[CAP];             // k-th segment with crossings
+  int aux[CAP];                       // first position of each segment in the current pass
   int q[kQueue];                      // crossings (segment | ordinal << 8) left to the exact path
   int qn;
   __device__ int cnt(int s, int a) const {
@@ -277,16 +282,17 @@ struct CoopSmem {
 };
 
 // Fill: the records expanded into per-field arrays (no unpacking per crossing)
-template <int DIM>
+template <int DIM, int CAP = kSegMax>
 struct FillSmem {
-  float4 ax[DIM][kSegMax];  // per axis: ph0, hv, 1 / hv, cb
-  int4 cn[kSegMax];         // crossings per axis (x, y, z), column of the start voxel (w)
-  int4 dc[kSegMax];         // signed column step per axis (x, y, z), first entry's CSR slot + 1 (w)
-  float4 sf[kSegMax];       // send, L, merged tail of the last entry, first entry's length
-  int misc[kSegMax];
+  static constexpr int kCap = CAP;
+  float4 ax[DIM][CAP];  // per axis: ph0, hv, 1 / hv, cb
+  int4 cn[CAP];         // crossings per axis (x, y, z), column of the start voxel (w)
+  int4 dc[CAP];         // signed column step per axis (x, y, z), first entry's CSR slot + 1 (w)
+  float4 sf[CAP];       // send, L, merged tail of the last entry, first entry's length
+  int misc[CAP];
   unsigned bits[kRowCross / 32 + 4];
-  unsigned char ord[kSegMax];
-  int aux[kSegMax];
+  unsigned char ord[CAP];
+  int aux[CAP];
   int q[kQueue];
   int qn;
   __device__ int cnt(int s, int a) const { return a == 0 ? cn[s].x : (a == 1 ? cn[s].y : cn[s].z); }
@@ -640,8 +646,8 @@ __device__ __forceinline__ int axis_starts(SM& sm, int nseg, int lane) {
   return t0 + t1;
 }
 
-template <int DIM, int A>
-__device__ __forceinline__ void tie_rows(CoopSmem<DIM>& sm, int nseg, int lane, const SimDev* Sg, const PathF64* p64,
+template <int DIM, int A, class SM>
+__device__ __forceinline__ void tie_rows(SM& sm, int nseg, int lane, const SimDev* Sg, const PathF64* p64,
                                          const int (&stride)[3], bool& tie, bool& overflow) {
   using W = SegW<DIM>;
   const int tot = axis_starts<A>(sm, nseg, lane);
@@ -688,8 +694,8 @@ struct FillOut {
 };
 
 // segment s of the fill's arrays as the exact path's view (axis A first)
-template <int DIM>
-__device__ __forceinline__ Axes<DIM> fill_axes(const FillSmem<DIM>& sm, int s, int a) {
+template <int DIM, class SM>
+__device__ __forceinline__ Axes<DIM> fill_axes(const SM& sm, int s, int a) {
   float p0[DIM], h[DIM], c[DIM];
   int n[DIM], d[DIM];
   const int4 cn = sm.cn[s], dc = sm.dc[s];
@@ -745,8 +751,8 @@ __device__ __forceinline__ void put_entry(const FillOut& F, int o, int c, float 
 // every crossing of axis A: one entry each.  Crossings the FP32 bounds
 // cannot settle are queued and redone exactly after the pass (no call in
 // the loop); *overflow when the queue was full.
-template <int DIM, int A>
-__device__ __forceinline__ void fill_axis(FillSmem<DIM>& sm, int nseg, int lane, const SimDev* Sg, const PathF64* p64,
+template <int DIM, int A, class SM>
+__device__ __forceinline__ void fill_axis(SM& sm, int nseg, int lane, const SimDev* Sg, const PathF64* p64,
                                           const FillOut& F, Kahan& wk, bool& overflow) {
   const int tot = axis_starts<A>(sm, nseg, lane);
   if (lane == 0) sm.qn = 0;
@@ -804,9 +810,9 @@ __device__ __forceinline__ void fill_axis(FillSmem<DIM>& sm, int nseg, int lane,
 // exact ties between crossings of different axes, writes the compact
 // segment records and the row's entry count.
 // ---------------------------------------------------------------------------
-template <int DIM>
+template <int DIM, class SM>
 __device__ __forceinline__ void coop_count_row(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
-                                               long long row, CoopSmem<DIM>& sm, long long* __restrict__ counts) {
+                                               long long row, SM& sm, long long* __restrict__ counts) {
   using W = SegW<DIM>;
   const int lane = threadIdx.x & 31;
   const GridDev& g = S.ph.g;
@@ -814,7 +820,7 @@ __device__ __forceinline__ void coop_count_row(const SimDev& S, const MixArgs& M
   const int nseg = r.nv - 1;
   const int stride[3] = {1, g.n[0], g.n[0] * (DIM > 2 ? g.n[1] : 1)};
   const PathF64* p64 = M.r64 + row;
-  bool irregular = nseg > kSegMax || nseg < 1 || nseg > M.seg_stride;
+  bool irregular = nseg > SM::kCap || nseg < 1 || nseg > M.seg_stride;
   if (!irregular) {
     // 1. segment table: lead segments from the pre-pass, interior ones here
     const SegP<DIM>* lead = lead_rec<DIM>(M, row);
@@ -929,9 +935,9 @@ __device__ __forceinline__ void coop_count_row(const SimDev& S, const MixArgs& M
 // plane after it, certified like the position) give one entry, written at
 // its CSR position; entry 0 of every segment comes from the segment's lane.
 // ---------------------------------------------------------------------------
-template <int DIM>
+template <int DIM, class SM>
 __device__ __forceinline__ void coop_fill_row(const SimDev& S, const MixArgs& M, const SimDev* Sg, long long row,
-                                              FillSmem<DIM>& sm, const long long* __restrict__ row_ptr,
+                                              SM& sm, const long long* __restrict__ row_ptr,
                                               const float* __restrict__ x, int* __restrict__ col,
                                               float* __restrict__ val, float* __restrict__ b) {
   using W = SegW<DIM>;
@@ -941,7 +947,7 @@ __device__ __forceinline__ void coop_fill_row(const SimDev& S, const MixArgs& M,
   const int nseg = r.nv - 1;
   const long long rowstart = row_ptr[row], rowend = row_ptr[row + 1];
   const SegG<DIM>* rec = (const SegG<DIM>*)M.segg + row * (long long)M.seg_stride;
-  bool irregular = nseg > kSegMax || nseg < 1 || nseg > M.seg_stride;
+  bool irregular = nseg > SM::kCap || nseg < 1 || nseg > M.seg_stride;
   if (!irregular) irregular = (reinterpret_cast<const int*>(rec)[W::MISC] & kRowIrregular) != 0;
   if (!irregular) {
     const int stride[3] = {1, g.n[0], g.n[0] * (DIM > 2 ? g.n[1] : 1)};

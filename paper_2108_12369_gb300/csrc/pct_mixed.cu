@@ -23,11 +23,14 @@ __device__ __forceinline__ SM& warp_smem() {
   return reinterpret_cast<SM*>(coop_dyn)[threadIdx.x >> 5];
 }
 
-// dynamic shared memory of a 128-thread count / fill block
-template <int DIM, bool kFill>
+// dynamic shared memory of a 128-thread count / fill block (rows of up to
+// CAP segments)
+template <int DIM, bool kFill, int CAP>
 constexpr size_t coop_bytes() {
-  return kFill ? 4 * sizeof(FillSmem<DIM>) : 4 * sizeof(CoopSmem<DIM>);
+  return kFill ? 4 * sizeof(FillSmem<DIM, CAP>) : 4 * sizeof(CoopSmem<DIM, CAP>);
 }
+
+bool small_cap(int seg_stride) { return seg_stride <= kSegSmall; }
 
 // Path phase of one block of 128 consecutive rows starting at row0: thread
 // t forms the FP64 path of row row0 + t (the definition), keeps it and its
@@ -69,10 +72,10 @@ __device__ __forceinline__ int next_row_of_block(int* take) {
 }
 
 // Count phase of the same block: each warp counts one row at a time.
-template <int DIM>
+template <int DIM, int CAP>
 __device__ __forceinline__ void rows_block(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
                                            long long n, long long row0, long long* __restrict__ counts) {
-  CoopSmem<DIM>& sm = warp_smem<CoopSmem<DIM>>();
+  CoopSmem<DIM, CAP>& sm = warp_smem<CoopSmem<DIM, CAP>>();
   __shared__ int take;
   if (threadIdx.x == 0) take = 4;
   __syncthreads();
@@ -89,20 +92,20 @@ __global__ void __launch_bounds__(128) k_path_mixed(SimDev S, MixArgs M, const S
   path_block<DIM>(S, M, Sg, gdg, n, (long long)blockIdx.x * blockDim.x);
 }
 
-template <int DIM>
+template <int DIM, int CAP>
 __global__ void __launch_bounds__(128, 8) k_count_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
                                                      long long n, long long* __restrict__ counts) {
-  rows_block<DIM>(S, M, Sg, gdg, n, (long long)blockIdx.x * blockDim.x, counts);
+  rows_block<DIM, CAP>(S, M, Sg, gdg, n, (long long)blockIdx.x * blockDim.x, counts);
 }
 
 // One block of 128 consecutive rows starting at row0 (fill phase): each
 // warp writes one row at a time.
-template <int DIM>
+template <int DIM, int CAP>
 __device__ __forceinline__ void fill_block(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
                                            long long n, long long row0, const long long* __restrict__ row_ptr,
                                            const float* __restrict__ x, int* __restrict__ col,
                                            float* __restrict__ val, float* __restrict__ b) {
-  FillSmem<DIM>& sm = warp_smem<FillSmem<DIM>>();
+  FillSmem<DIM, CAP>& sm = warp_smem<FillSmem<DIM, CAP>>();
   const int lane = threadIdx.x & 31;
   const int lines = (M.seg_stride * (int)sizeof(SegG<DIM>) + 127) / 128;
   __shared__ int take;
@@ -124,24 +127,24 @@ __device__ __forceinline__ void fill_block(const SimDev& S, const MixArgs& M, co
   }
 }
 
-template <int DIM>
+template <int DIM, int CAP>
 __global__ void __launch_bounds__(128, 7) k_fill_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
                                                     long long n, const long long* __restrict__ row_ptr,
                                                     const float* __restrict__ x, int* __restrict__ col,
                                                     float* __restrict__ val, float* __restrict__ b) {
-  fill_block<DIM>(S, M, Sg, gdg, n, (long long)blockIdx.x * blockDim.x, row_ptr, x, col, val, b);
+  fill_block<DIM, CAP>(S, M, Sg, gdg, n, (long long)blockIdx.x * blockDim.x, row_ptr, x, col, val, b);
 }
 
 // rows [row_begin, n) only (a kernel of its own, so that the whole fill
 // keeps its first row at compile-time zero)
-template <int DIM>
+template <int DIM, int CAP>
 __global__ void __launch_bounds__(128, 7) k_fill_mixed_range(SimDev S, MixArgs M, const SimDev* Sg,
                                                           const GridDF* gdg, long long n,
                                                           const long long* __restrict__ row_ptr,
                                                           const float* __restrict__ x, int* __restrict__ col,
                                                           float* __restrict__ val, float* __restrict__ b,
                                                           long long row_begin) {
-  fill_block<DIM>(S, M, Sg, gdg, n, row_begin + (long long)blockIdx.x * blockDim.x, row_ptr, x, col, val, b);
+  fill_block<DIM, CAP>(S, M, Sg, gdg, n, row_begin + (long long)blockIdx.x * blockDim.x, row_ptr, x, col, val, b);
 }
 
 // ---------------------------------------------------------------------------
@@ -163,7 +166,7 @@ __device__ __forceinline__ int batch_find(const BatchInst* __restrict__ B, int n
 
 // phases: 0 path set-up, 1 count, 2 fill (the launch bounds follow the
 // per-simulation kernels of each phase)
-template <int kPhase, int DIM>
+template <int kPhase, int DIM, int CAP>
 __global__ void __launch_bounds__(128, kPhase == 0 ? 1 : (kPhase == 1 ? 8 : 7))
     k_batch(const BatchInst* __restrict__ B, int n_inst, long long first, long long last,
             unsigned long long* next) {
@@ -177,9 +180,9 @@ __global__ void __launch_bounds__(128, kPhase == 0 ? 1 : (kPhase == 1 ? 8 : 7))
     const BatchInst& I = B[batch_find(B, n_inst, item)];
     const long long row0 = (item - I.item0) * 128;
     if constexpr (kPhase == 2)
-      fill_block<DIM>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, I.row_ptr, I.x, I.col, I.val, I.b);
+      fill_block<DIM, CAP>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, I.row_ptr, I.x, I.col, I.val, I.b);
     else if constexpr (kPhase == 1)
-      rows_block<DIM>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, I.row_ptr_w + 1);
+      rows_block<DIM, CAP>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, I.row_ptr_w + 1);
     else
       path_block<DIM>(I.S, I.M, &I.S, &I.M.gd, I.n, row0);
   }
@@ -191,42 +194,56 @@ static void smem_attr(Kern k, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int kPhase, int DIM>
+template <int kPhase, int DIM, int CAP>
 static size_t batch_smem() {
-  return kPhase == 0 ? 0 : coop_bytes<DIM, kPhase == 2>();
+  return kPhase == 0 ? 0 : coop_bytes<DIM, kPhase == 2, CAP>();
 }
 
-template <int kPhase, int DIM>
+template <int kPhase, int DIM, int CAP>
 static int blocks_per_sm() {
   int nb = 0;
-  smem_attr(k_batch<kPhase, DIM>, batch_smem<kPhase, DIM>());
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<kPhase, DIM>, 128, batch_smem<kPhase, DIM>());
+  smem_attr(k_batch<kPhase, DIM, CAP>, batch_smem<kPhase, DIM, CAP>());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<kPhase, DIM, CAP>, 128, batch_smem<kPhase, DIM, CAP>());
   return nb > 0 ? nb : 1;
 }
 
-int batch_blocks_per_sm(int phase, int dim) {
-  if (phase == 0) return dim == 2 ? blocks_per_sm<0, 2>() : blocks_per_sm<0, 3>();
-  if (phase == 1) return dim == 2 ? blocks_per_sm<1, 2>() : blocks_per_sm<1, 3>();
-  return dim == 2 ? blocks_per_sm<2, 2>() : blocks_per_sm<2, 3>();
+// (the path phase has no shared memory: one capacity serves every batch)
+int batch_blocks_per_sm(int phase, int dim, bool small) {
+  if (phase == 0) return dim == 2 ? blocks_per_sm<0, 2, kSegMax>() : blocks_per_sm<0, 3, kSegMax>();
+  if (phase == 1) {
+    if (small) return dim == 2 ? blocks_per_sm<1, 2, kSegSmall>() : blocks_per_sm<1, 3, kSegSmall>();
+    return dim == 2 ? blocks_per_sm<1, 2, kSegMax>() : blocks_per_sm<1, 3, kSegMax>();
+  }
+  if (small) return dim == 2 ? blocks_per_sm<2, 2, kSegSmall>() : blocks_per_sm<2, 3, kSegSmall>();
+  return dim == 2 ? blocks_per_sm<2, 2, kSegMax>() : blocks_per_sm<2, 3, kSegMax>();
+}
+
+template <int kPhase, int DIM, int CAP>
+static void launch_phase(const BatchInst* B, int n_inst, long long first, long long last, unsigned long long* next,
+                         int grid, cudaStream_t st) {
+  smem_attr(k_batch<kPhase, DIM, CAP>, batch_smem<kPhase, DIM, CAP>());
+  k_batch<kPhase, DIM, CAP><<<grid, 128, batch_smem<kPhase, DIM, CAP>(), st>>>(B, n_inst, first, last, next);
 }
 
 template <int kPhase, int DIM>
-static void launch_phase(const BatchInst* B, int n_inst, long long first, long long last, unsigned long long* next,
-                         int grid, cudaStream_t st) {
-  smem_attr(k_batch<kPhase, DIM>, batch_smem<kPhase, DIM>());
-  k_batch<kPhase, DIM><<<grid, 128, batch_smem<kPhase, DIM>(), st>>>(B, n_inst, first, last, next);
+static void launch_phase_cap(bool small, const BatchInst* B, int n_inst, long long first, long long last,
+                             unsigned long long* next, int grid, cudaStream_t st) {
+  if (kPhase == 0 || !small)
+    launch_phase<kPhase, DIM, kSegMax>(B, n_inst, first, last, next, grid, st);
+  else
+    launch_phase<kPhase, DIM, kSegSmall>(B, n_inst, first, last, next, grid, st);
 }
 
-void launch_batch(int phase, int dim, const BatchInst* B, int n_inst, long long first, long long last,
+void launch_batch(int phase, int dim, bool small, const BatchInst* B, int n_inst, long long first, long long last,
                   unsigned long long* next, int grid, cudaStream_t st) {
   cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
   if (last <= first || n_inst <= 0) return;
-  if (phase == 0 && dim == 2) launch_phase<0, 2>(B, n_inst, first, last, next, grid, st);
-  if (phase == 0 && dim == 3) launch_phase<0, 3>(B, n_inst, first, last, next, grid, st);
-  if (phase == 1 && dim == 2) launch_phase<1, 2>(B, n_inst, first, last, next, grid, st);
-  if (phase == 1 && dim == 3) launch_phase<1, 3>(B, n_inst, first, last, next, grid, st);
-  if (phase == 2 && dim == 2) launch_phase<2, 2>(B, n_inst, first, last, next, grid, st);
-  if (phase == 2 && dim == 3) launch_phase<2, 3>(B, n_inst, first, last, next, grid, st);
+  if (phase == 0 && dim == 2) launch_phase_cap<0, 2>(small, B, n_inst, first, last, next, grid, st);
+  if (phase == 0 && dim == 3) launch_phase_cap<0, 3>(small, B, n_inst, first, last, next, grid, st);
+  if (phase == 1 && dim == 2) launch_phase_cap<1, 2>(small, B, n_inst, first, last, next, grid, st);
+  if (phase == 1 && dim == 3) launch_phase_cap<1, 3>(small, B, n_inst, first, last, next, grid, st);
+  if (phase == 2 && dim == 2) launch_phase_cap<2, 2>(small, B, n_inst, first, last, next, grid, st);
+  if (phase == 2 && dim == 3) launch_phase_cap<2, 3>(small, B, n_inst, first, last, next, grid, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -354,6 +371,34 @@ static bool upload_args(const SimDev& S, const MixArgs& M, void* args, cudaStrea
          cudaMemcpyAsync(base + off, &M.gd, sizeof(GridDF), cudaMemcpyHostToDevice, st) == cudaSuccess;
 }
 
+// the count / fill kernels for rows of up to kSegSmall (small) or kSegMax segments
+template <int DIM>
+static void launch_count_cap(bool small, unsigned blocks, const SimDev& S, const MixArgs& M, const SimDev* Sg,
+                             const GridDF* gdg, long long n, long long* counts, cudaStream_t st) {
+  if (small) {
+    smem_attr(k_count_mixed<DIM, kSegSmall>, coop_bytes<DIM, false, kSegSmall>());
+    k_count_mixed<DIM, kSegSmall><<<blocks, 128, coop_bytes<DIM, false, kSegSmall>(), st>>>(S, M, Sg, gdg, n, counts);
+  } else {
+    smem_attr(k_count_mixed<DIM, kSegMax>, coop_bytes<DIM, false, kSegMax>());
+    k_count_mixed<DIM, kSegMax><<<blocks, 128, coop_bytes<DIM, false, kSegMax>(), st>>>(S, M, Sg, gdg, n, counts);
+  }
+}
+
+template <int DIM, int CAP>
+static void launch_fill_cap(bool whole, unsigned blocks, const SimDev& S, const MixArgs& M, const SimDev* Sg,
+                            const GridDF* gdg, long long n, long long row_end, long long row_begin,
+                            const long long* row_ptr, const float* x, int* col, float* val, float* b,
+                            cudaStream_t st) {
+  const size_t sm = coop_bytes<DIM, true, CAP>();
+  if (whole) {
+    smem_attr(k_fill_mixed<DIM, CAP>, sm);
+    k_fill_mixed<DIM, CAP><<<blocks, 128, sm, st>>>(S, M, Sg, gdg, n, row_ptr, x, col, val, b);
+  } else {
+    smem_attr(k_fill_mixed_range<DIM, CAP>, sm);
+    k_fill_mixed_range<DIM, CAP><<<blocks, 128, sm, st>>>(S, M, Sg, gdg, row_end, row_ptr, x, col, val, b, row_begin);
+  }
+}
+
 void launch_count_mixed(const SimDev& S, const void* tab, long long n, void* rec, long long* counts, void* args,
                         cudaStream_t st) {
   if (n <= 0) return;
@@ -363,12 +408,13 @@ void launch_count_mixed(const SimDev& S, const void* tab, long long n, void* rec
   if (!upload_args(S, M, args, st, &Sg, &gdg)) return;
   int threads = 128;
   unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  const bool small = small_cap(M.seg_stride);
   if (S.ph.g.dim == 2) {
     k_path_mixed<2><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n);
-    k_count_mixed<2><<<blocks, threads, coop_bytes<2, false>(), st>>>(S, M, Sg, gdg, n, counts);
+    launch_count_cap<2>(small, blocks, S, M, Sg, gdg, n, counts, st);
   } else {
     k_path_mixed<3><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n);
-    k_count_mixed<3><<<blocks, threads, coop_bytes<3, false>(), st>>>(S, M, Sg, gdg, n, counts);
+    launch_count_cap<3>(small, blocks, S, M, Sg, gdg, n, counts, st);
   }
 }
 
@@ -395,24 +441,17 @@ void launch_fill_mixed(const SimDev& S, const void* tab, long long n, const void
   col = (int*)((uintptr_t)col - sizeof(int) * (uintptr_t)nz0);
   val = (float*)((uintptr_t)val - sizeof(float) * (uintptr_t)nz0);
   b = (float*)((uintptr_t)b - sizeof(float) * (uintptr_t)row_begin);
+  const bool small = small_cap(M.seg_stride);
   if (S.ph.g.dim == 2) {
-    if (whole) {
-      smem_attr(k_fill_mixed<2>, coop_bytes<2, true>());
-      k_fill_mixed<2><<<blocks, threads, coop_bytes<2, true>(), st>>>(S, M, Sg, gdg, n, row_ptr, x, col, val, b);
-    } else {
-      smem_attr(k_fill_mixed_range<2>, coop_bytes<2, true>());
-      k_fill_mixed_range<2><<<blocks, threads, coop_bytes<2, true>(), st>>>(S, M, Sg, gdg, row_end, row_ptr, x, col,
-                                                                          val, b, row_begin);
-    }
+    if (small)
+      launch_fill_cap<2, kSegSmall>(whole, blocks, S, M, Sg, gdg, n, row_end, row_begin, row_ptr, x, col, val, b, st);
+    else
+      launch_fill_cap<2, kSegMax>(whole, blocks, S, M, Sg, gdg, n, row_end, row_begin, row_ptr, x, col, val, b, st);
   } else {
-    if (whole) {
-      smem_attr(k_fill_mixed<3>, coop_bytes<3, true>());
-      k_fill_mixed<3><<<blocks, threads, coop_bytes<3, true>(), st>>>(S, M, Sg, gdg, n, row_ptr, x, col, val, b);
-    } else {
-      smem_attr(k_fill_mixed_range<3>, coop_bytes<3, true>());
-      k_fill_mixed_range<3><<<blocks, threads, coop_bytes<3, true>(), st>>>(S, M, Sg, gdg, row_end, row_ptr, x, col,
-                                                                          val, b, row_begin);
-    }
+    if (small)
+      launch_fill_cap<3, kSegSmall>(whole, blocks, S, M, Sg, gdg, n, row_end, row_begin, row_ptr, x, col, val, b, st);
+    else
+      launch_fill_cap<3, kSegMax>(whole, blocks, S, M, Sg, gdg, n, row_end, row_begin, row_ptr, x, col, val, b, st);
   }
 }
 

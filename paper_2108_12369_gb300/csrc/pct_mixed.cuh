@@ -674,8 +674,12 @@ struct BatchInst {
 MixArgs mix_args(const SimDev& S, long long n, const void* tab, void* rec);
 // persistent launch of one phase (0 path set-up, 1 count, 2 fill) over the
 // items [first, last) (all of dimension dim)
-int batch_blocks_per_sm(int phase, int dim);
-void launch_batch(int phase, int dim, const BatchInst* B, int n_inst, long long first, long long last,
+// whether rows of up to seg_stride segments fit the smaller per-warp
+// shared-memory layout of the count / fill kernels
+bool small_cap(int seg_stride);
+// small: every instance of that dimension fits the smaller layout
+int batch_blocks_per_sm(int phase, int dim, bool small);
+void launch_batch(int phase, int dim, bool small, const BatchInst* B, int n_inst, long long first, long long last,
                   unsigned long long* next, int grid, cudaStream_t st);
 
 }  // namespace pct
