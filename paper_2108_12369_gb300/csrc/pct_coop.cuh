@@ -258,7 +258,7 @@ __device__ __forceinline__ SegR<DIM> pack_seg(const SegP<DIM>& p) {
 }
 
 constexpr int kSegMax = 64;     // segments of one row handled cooperatively (at most)
-constexpr int kSegSmall = 40;   // the smaller per-warp capacity (splines of up to 38 pieces)
+constexpr int kSegSmall = 36;   // the smaller per-warp capacity (splines of up to 34 pieces)
 constexpr int kRowCross = 4096; // crossings of one row handled cooperatively
 
 constexpr int kQueue = 32;  // crossings per pass left to the exact path
