@@ -185,3 +185,16 @@ def test_rows_beyond_cooperative_limits(pct, orc):
     ref = run_oracle(orc, w)
     assert np.diff(ref["row_ptr"]).min() > 4096
     compare(g, ref)
+
+
+@pytest.mark.parametrize("K", [34, 35, 48])
+def test_both_shared_memory_layouts(pct, orc, K):
+    """Splines of 34 pieces (36 segments: the smaller per-warp layout, full)
+    and of 35 and 48 pieces (37 and 50 segments: the 64-segment layout), 2D
+    and 3D, against the oracle."""
+    w = W.neo2_2d_spline(n_angles=6, paths_per_angle=150, n=128, h=1.6)
+    w["model"] = dict(w["model"], spline_segments=K)
+    compare(run_gpu(pct, w, "mixed"), run_oracle(orc, w))
+    w = W.head_3d_spline(n_angles=3, paths_per_angle=200, n=(40, 40, 32), h=(2.0, 2.0, 2.0))
+    w["model"] = dict(w["model"], spline_segments=K)
+    compare(run_gpu(pct, w, "mixed"), run_oracle(orc, w))
