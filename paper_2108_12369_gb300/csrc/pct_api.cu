@@ -693,7 +693,7 @@ extern "C" pct_status pct_batch_create(const pct_batch_item* items, int32_t n, v
     I.row_ptr_w = (long long*)items[k].row_ptr_dev;
     I.row_ptr = (const long long*)items[k].row_ptr_dev;
     I.x = items[k].x_true_dev;
-    if (!small_cap(I.M.seg_stride)) b->small[I.S.ph.g.dim == 3 ? 1 : 0] = false;
+    if (!small_cap(I.M.seg_stride, I.S.ph.g)) b->small[I.S.ph.g.dim == 3 ? 1 : 0] = false;
   }
   for (int f = 0; f < 3; ++f)
     for (int d = 0; d < 2; ++d) b->bps[f][d] = batch_blocks_per_sm(f, d == 0 ? 2 : 3, b->small[d]);

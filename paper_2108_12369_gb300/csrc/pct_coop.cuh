@@ -21,8 +21,8 @@
 // line).  Decisions, voxel indices, lengths and merges are those of the
 // per-lane walker.  Rows with an exact tie between crossings of different
 // axes, a segment that needs the FP64 walk, more segments than the warp's
-// shared-memory capacity (kSegMax at most) or more than kRowCross crossings
-// are handed to the per-lane walker (lane 0 of the warp); the count marks
+// shared-memory capacity (kSegMax at most) or more crossings than it holds
+// (kRowCross at most) are handed to the per-lane walker (lane 0 of the warp); the count marks
 // them for the fill.
 #pragma once
 #include "pct_walk.cuh"
@@ -262,6 +262,10 @@ constexpr int kSegSmall = 36;   // the smaller per-warp capacity (splines of up 
 constexpr int kRowCross = 4096; // crossings of one row handled cooperatively
 
 constexpr int kQueue = 32;  // crossings per pass left to the exact path
+// the smaller per-warp layout (kSegSmall segments) also holds fewer crossings
+// and queue entries: rows beyond them take the per-lane walker
+constexpr int kRowCrossSmall = 2048;
+constexpr int kQueueSmall = 16;
 
 // Count: the row's segment records plus the crossing enumeration, for rows
 // of up to CAP segments (a smaller CAP leaves more of the SM's on-chip
@@ -269,11 +273,13 @@ constexpr int kQueue = 32;  // crossings per pass left to the exact path
 template <int DIM, int CAP = kSegMax>
 struct CoopSmem {
   static constexpr int kCap = CAP;
+  static constexpr int kCross = CAP <= kSegSmall ? kRowCrossSmall : kRowCross;
+  static constexpr int kQ = CAP <= kSegSmall ? kQueueSmall : kQueue;
   SegG<DIM> tab[CAP];
-  unsigned bits[kRowCross / 32 + 4];  // segment starts among the row's crossings
+  unsigned bits[kCross / 32 + 4];  // segment starts among the row's crossings
   unsigned char ord[CAP];             // k-th segment with crossings
   int aux[CAP];                       // first position of each segment in the current pass
-  int q[kQueue];                      // crossings (segment | ordinal << 8) left to the exact path
+  int q[kQ];                          // crossings (segment | ordinal << 8) left to the exact path
   int qn;
   __device__ int cnt(int s, int a) const {
     const int w = reinterpret_cast<const int*>(&tab[s])[SegW<DIM>::CNT + (a >> 1)];
@@ -285,15 +291,17 @@ struct CoopSmem {
 template <int DIM, int CAP = kSegMax>
 struct FillSmem {
   static constexpr int kCap = CAP;
+  static constexpr int kCross = CAP <= kSegSmall ? kRowCrossSmall : kRowCross;
+  static constexpr int kQ = CAP <= kSegSmall ? kQueueSmall : kQueue;
   float4 ax[DIM][CAP];  // per axis: ph0, hv, 1 / hv, cb
   int4 cn[CAP];         // crossings per axis (x, y, z), column of the start voxel (w)
   int4 dc[CAP];         // signed column step per axis (x, y, z), first entry's CSR slot + 1 (w)
   float4 sf[CAP];       // send, L, merged tail of the last entry, first entry's length
   int misc[CAP];
-  unsigned bits[kRowCross / 32 + 4];
+  unsigned bits[kCross / 32 + 4];
   unsigned char ord[CAP];
   int aux[CAP];
-  int q[kQueue];
+  int q[kQ];
   int qn;
   __device__ int cnt(int s, int a) const { return a == 0 ? cn[s].x : (a == 1 ? cn[s].y : cn[s].z); }
 };
@@ -664,7 +672,7 @@ __device__ __forceinline__ void tie_rows(SM& sm, int nseg, int lane, const SimDe
       tie_axis<DIM, A>(R, i, unsure);
       if (unsure) {
         const int k = atomicAdd(&sm.qn, 1);
-        if (k < kQueue)
+        if (k < SM::kQ)
           sm.q[k] = s | (i << 8);
         else
           overflow = true;
@@ -673,7 +681,7 @@ __device__ __forceinline__ void tie_rows(SM& sm, int nseg, int lane, const SimDe
   }
   __syncwarp();
   // the crossings the FP32 bounds could not settle
-  const int nq = min(sm.qn, kQueue);
+  const int nq = min(sm.qn, SM::kQ);
   for (int k = lane; k < nq; k += 32) {
     const int s = sm.q[k] & 0xff, i = sm.q[k] >> 8;
     const SegR<DIM> R = load_seg<DIM>(sm.tab[s]);
@@ -780,7 +788,7 @@ __device__ __forceinline__ void fill_axis(SM& sm, int nseg, int lane, const SimD
         xv = put_entry_x(F, dc.w + cr.rank, cr.colv, v);
       } else {
         const int k = atomicAdd(&sm.qn, 1);
-        if (k < kQueue)
+        if (k < SM::kQ)
           sm.q[k] = s | (i << 8);
         else
           overflow = true;
@@ -792,7 +800,7 @@ __device__ __forceinline__ void fill_axis(SM& sm, int nseg, int lane, const SimD
   }
   wk.add(pv * px);
   __syncwarp();
-  const int nq = min(sm.qn, kQueue);
+  const int nq = min(sm.qn, SM::kQ);
   for (int k = lane; k < nq; k += 32) {
     const int s = sm.q[k] & 0xff, i = sm.q[k] >> 8;
     const float4 sf = sm.sf[s];
@@ -877,7 +885,7 @@ __device__ __forceinline__ void coop_count_row(const SimDev& S, const MixArgs& M
     eb[0] = warp_excl_scan(Es[0], lane, &t0);
     eb[1] = warp_excl_scan(Es[1], lane, &t1) + t0;
     const int totE = t0 + t1;
-    bad |= totC > kRowCross;
+    bad |= totC > SM::kCross;
     irregular = __any_sync(0xffffffffu, bad) != 0;
     __syncwarp();
 #pragma unroll
@@ -976,7 +984,7 @@ __device__ __forceinline__ void coop_fill_row(const SimDev& S, const MixArgs& M,
     }
     __syncwarp();
     const int totC = __reduce_add_sync(0xffffffffu, Cs[0] + Cs[1]);
-    if (totC <= kRowCross) {
+    if (totC <= SM::kCross) {
       Kahan wk{0.f, 0.f};
       FillOut F;
       F.col = col + rowstart;

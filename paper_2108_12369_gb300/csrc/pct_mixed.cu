@@ -30,7 +30,13 @@ constexpr size_t coop_bytes() {
   return kFill ? 4 * sizeof(FillSmem<DIM, CAP>) : 4 * sizeof(CoopSmem<DIM, CAP>);
 }
 
-bool small_cap(int seg_stride) { return seg_stride <= kSegSmall; }
+// the smaller layout: rows of up to kSegSmall segments on grids whose
+// straight lines cross at most 1536 planes (rows then stay well below
+// kRowCrossSmall crossings; longer ones take the walker all the same)
+bool small_cap(int seg_stride, const GridDev& g) {
+  const int planes = g.n[0] + g.n[1] + (g.dim == 3 ? g.n[2] : 0);
+  return seg_stride <= kSegSmall && planes <= 1536;
+}
 
 // Path phase of one block of 128 consecutive rows starting at row0: thread
 // t forms the FP64 path of row row0 + t (the definition), keeps it and its
@@ -408,7 +414,7 @@ void launch_count_mixed(const SimDev& S, const void* tab, long long n, void* rec
   if (!upload_args(S, M, args, st, &Sg, &gdg)) return;
   int threads = 128;
   unsigned blocks = (unsigned)((n + threads - 1) / threads);
-  const bool small = small_cap(M.seg_stride);
+  const bool small = small_cap(M.seg_stride, S.ph.g);
   if (S.ph.g.dim == 2) {
     k_path_mixed<2><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n);
     launch_count_cap<2>(small, blocks, S, M, Sg, gdg, n, counts, st);
@@ -441,7 +447,7 @@ void launch_fill_mixed(const SimDev& S, const void* tab, long long n, const void
   col = (int*)((uintptr_t)col - sizeof(int) * (uintptr_t)nz0);
   val = (float*)((uintptr_t)val - sizeof(float) * (uintptr_t)nz0);
   b = (float*)((uintptr_t)b - sizeof(float) * (uintptr_t)row_begin);
-  const bool small = small_cap(M.seg_stride);
+  const bool small = small_cap(M.seg_stride, S.ph.g);
   if (S.ph.g.dim == 2) {
     if (small)
       launch_fill_cap<2, kSegSmall>(whole, blocks, S, M, Sg, gdg, n, row_end, row_begin, row_ptr, x, col, val, b, st);

@@ -674,9 +674,9 @@ struct BatchInst {
 MixArgs mix_args(const SimDev& S, long long n, const void* tab, void* rec);
 // persistent launch of one phase (0 path set-up, 1 count, 2 fill) over the
 // items [first, last) (all of dimension dim)
-// whether rows of up to seg_stride segments fit the smaller per-warp
-// shared-memory layout of the count / fill kernels
-bool small_cap(int seg_stride);
+// whether a simulation (rows of up to seg_stride segments, grid g) takes the
+// smaller per-warp shared-memory layout of the count / fill kernels
+bool small_cap(int seg_stride, const GridDev& g);
 // small: every instance of that dimension fits the smaller layout
 int batch_blocks_per_sm(int phase, int dim, bool small);
 void launch_batch(int phase, int dim, bool small, const BatchInst* B, int n_inst, long long first, long long last,
