@@ -320,13 +320,17 @@ extern "C" pct_status pct_simulate_fill_host(const pct_phantom* ph, const pct_ge
                                              int64_t* row_ptr_host, int32_t* col_host, float* val_host,
                                              float* b_host, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
+  // argument checks first (host only)
+  pct_status rc = check_geometry(ph, g, precision);
+  if (rc != PCT_OK) return rc;
+  const long long rows = layout_of(ph, g, precision).rows;
+  if (!row_ptr_dev || !row_ptr_host) return fail(PCT_EINVAL, "pct_simulate_fill_host: NULL row pointers");
+  if (rows > 0 && (!x || !b_host || !staging)) return fail(PCT_EINVAL, "pct_simulate_fill_host: NULL argument");
+  if ((uintptr_t)staging % 256 != 0) return fail(PCT_EINVAL, "staging buffer must be 256-byte aligned");
   SimDev S;
   Layout L;
-  pct_status rc = make_sim(ph, g, precision, ws, ws_bytes, st, S, L);
+  rc = make_sim(ph, g, precision, ws, ws_bytes, st, S, L);
   if (rc != PCT_OK) return rc;
-  if (!row_ptr_dev || !row_ptr_host) return fail(PCT_EINVAL, "pct_simulate_fill_host: NULL row pointers");
-  if (L.rows > 0 && (!x || !b_host || !staging)) return fail(PCT_EINVAL, "pct_simulate_fill_host: NULL argument");
-  if ((uintptr_t)staging % 256 != 0) return fail(PCT_EINVAL, "staging buffer must be 256-byte aligned");
   // each half: E col entries, E val entries, E / 16 b values (E a multiple of 64)
   const long long half = (long long)(staging_bytes / 2) & ~255LL;
   const long long E = (long long)((double)half / 8.25) & ~63LL;

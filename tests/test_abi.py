@@ -89,3 +89,22 @@ def test_batch_workspace_size_validates(pct):
     with pytest.raises(pct.PctError) as e:
         pct.batch_workspace_size(bad)
     assert e.value.status == pct.EINVAL
+
+
+def test_fill_host_validates_before_any_device_work(pct):
+    """pct_simulate_fill_host checks its pointers on the host (no GPU needed)."""
+    w = W.neo2_2d_spline(n_angles=2, paths_per_angle=10, n=64, h=3.2)
+    ph, geo = pct.Phantom(w["phantom"]), pct.GeometryArgs(w)
+    L = pct.lib()
+    st = L.pct_simulate_fill_host(ph.handle, C.byref(geo.c), pct.PREC_MIXED, None, 0, None, None, None, 0,
+                                  None, None, None, None, None)
+    assert st == pct.EINVAL and b"NULL row pointers" in L.pct_last_error()
+    buf = (C.c_int64 * 64)()
+    p = C.cast(buf, C.c_void_p)
+    st = L.pct_simulate_fill_host(ph.handle, C.byref(geo.c), pct.PREC_MIXED, None, 0, p, None, None, 0,
+                                  p, None, None, None, None)
+    assert st == pct.EINVAL and b"NULL argument" in L.pct_last_error()
+    odd = C.c_void_p((p.value + 255) // 256 * 256 + 8)  # not 256-byte aligned (never dereferenced)
+    st = L.pct_simulate_fill_host(ph.handle, C.byref(geo.c), pct.PREC_MIXED, None, 0, p, p, odd, 1 << 20,
+                                  p, p, p, p, None)
+    assert st == pct.EINVAL and b"aligned" in L.pct_last_error()
