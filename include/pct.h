@@ -45,7 +45,7 @@ typedef enum {
   PCT_EINVAL = 1,       /* bad argument: nothing was enqueued */
   PCT_ENOMEM = 2,       /* the caller's allocator returned NULL / workspace too small */
   PCT_ECUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
-  PCT_ETIMEOUT = 4,     /* a device-side bounded wait ran out */
+  PCT_ETIMEOUT = 4,     /* reserved: no call returns it (no kernel of the library waits on another) */
   PCT_EUNSUPPORTED = 5  /* valid request the library does not implement */
 } pct_status;
 
@@ -108,10 +108,17 @@ typedef struct {
   double noise_rel;
 } pct_path_model;
 
-/* One simulated acquisition: angles (host, radians), protons per angle, the
- * path model, and the generator key (seed, stream_id).  Random numbers come
- * from Philox4x64-10 (Salmon et al., SC'11) with key (seed, stream_id) and
- * counter (row, block, 0, 0), replacing the paper's rand(). */
+/* One simulated acquisition, or a contiguous block of one: angles (host,
+ * radians), protons per angle, the path model, the generator key (seed,
+ * stream_id) and the global index of its first row.  Random numbers come from
+ * Philox4x64-10 (Salmon et al., SC'11) with key (seed, stream_id) and counter
+ * (first_row + i, block, 0, 0) for row i of the call, replacing the paper's
+ * rand().  A block of angles [k0, k1) of an acquisition with P protons per
+ * angle (Sec. IV: an acquisition-structured partition over GPUs) passes
+ * angles_rad + k0, n_angles = k1 - k0 and first_row = k0 P: its rows are then
+ * bit for bit rows k0 P .. k1 P - 1 of the whole acquisition, and the blocks'
+ * CSRs concatenate into the whole one.  first_row = 0 for a whole
+ * acquisition; 0 <= first_row, first_row + rows <= 2^62. */
 typedef struct {
   const double* angles_rad;
   int32_t n_angles;
@@ -119,6 +126,7 @@ typedef struct {
   pct_path_model model;
   uint64_t seed;
   uint64_t stream_id;
+  int64_t first_row;
 } pct_geometry;
 
 typedef struct pct_phantom pct_phantom; /* opaque, host memory only */
@@ -288,10 +296,12 @@ pct_status pct_batch_destroy(pct_batch* batch);
  * inside pct_simulate_count, without a workspace.  The scratch (one int64 per
  * tile of rows) is a static device array sized for PCT_STATIC_SCAN_MAX_ROWS
  * rows, 512 KB that every GPU loading this library holds until the process
- * exits; larger n_rows return PCT_EINVAL with a message.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress, on the
- * calling thread's current device); make that first call before any stream
- * capture.  All calls share the one array: calls whose work overlaps on the
+ * exits; larger n_rows return PCT_EINVAL with a message.  Every call looks up
+ * that array's device address for the calling thread's current device
+ * (cudaGetSymbolAddress, which allocates nothing), so the address stays right
+ * after a cudaDeviceReset or in another context; the first call on a device
+ * also loads the module that holds the array, so make that first call before
+ * any stream capture.  All calls share the one array: calls whose work overlaps on the
  * GPU (other streams, other threads) race and corrupt each other's results --
  * serialise them.  A call writes every scratch slot it reads, so nothing has to
  * be cleared between calls.  No cudaMalloc, cudaFree or allocating library

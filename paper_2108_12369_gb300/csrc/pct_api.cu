@@ -152,6 +152,8 @@ pct_status check_geometry(const pct_phantom* ph, const pct_geometry* g, int prec
   long long rows = (long long)g->n_angles * g->paths_per_angle;
   if (g->paths_per_angle > 0 && rows / g->paths_per_angle != g->n_angles) return fail(PCT_EINVAL, "row count overflows");
   if (rows > (1LL << 40)) return fail(PCT_EINVAL, "more than 2^40 rows");
+  if (g->first_row < 0 || g->first_row > (1LL << 62) - rows)
+    return fail(PCT_EINVAL, "first_row = %lld outside [0, 2^62 - rows]", (long long)g->first_row);
   const pct_path_model& m = g->model;
   if (m.model < PCT_PATH_STRAIGHT || m.model > PCT_PATH_SPLINE) return fail(PCT_EINVAL, "bad path model %d", m.model);
   if (m.chord != PCT_CHORD_EXACT && m.chord != PCT_CHORD_CONSTANT) return fail(PCT_EINVAL, "bad chord option %d", m.chord);
@@ -223,6 +225,7 @@ pct_status make_sim(const pct_phantom* ph, const pct_geometry* g, int precision,
   S.P = g->paths_per_angle;
   S.seed = g->seed;
   S.stream = g->stream_id;
+  S.first_row = g->first_row;
   double diag2 = 0.0;
   for (int a = 0; a < ph->dev.g.dim; ++a) {
     double w = (double)ph->dev.g.n[a] * ph->dev.g.h[a];
@@ -342,6 +345,8 @@ extern "C" pct_status pct_simulate_fill_host(const pct_phantom* ph, const pct_ge
   if (L.rows == 0) return PCT_OK;
   if (E < 64) return fail(PCT_EINVAL, "staging buffer of %zu bytes is too small", staging_bytes);
   const long long* rph = (const long long*)row_ptr_host;
+  if (rph[L.rows] > 0 && (!col_host || !val_host))
+    return fail(PCT_EINVAL, "pct_simulate_fill_host: NULL col_host or val_host for %lld nonzeros", rph[L.rows]);
   cudaStream_t cs = nullptr;
   cudaEvent_t ev_fill[2] = {nullptr, nullptr}, ev_copy[2] = {nullptr, nullptr};
   auto cleanup = [&]() {
@@ -379,6 +384,7 @@ extern "C" pct_status pct_simulate_fill_host(const pct_phantom* ph, const pct_ge
     float* val_s = (float*)(base + h * half + 4 * E);
     float* b_s = (float*)(base + h * half + 8 * E);
     if (k >= 2) ok = cudaStreamWaitEvent(st, ev_copy[h], 0) == cudaSuccess;
+    if (!ok) break;  // never refill a half whose copy may still be running
     if (precision == PCT_PREC_F64)  // col / val by CSR position: bases moved back by nz0 (host arithmetic)
       launch_fill_f64(S, r0, r1 - r0, (const long long*)row_ptr_dev + r0, x,
                       (int*)((uintptr_t)col_s - sizeof(int) * (uintptr_t)nz0),

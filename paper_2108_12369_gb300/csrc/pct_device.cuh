@@ -56,6 +56,7 @@ struct SimDev {
   int n_angles;
   long long P;  // paths per angle
   unsigned long long seed, stream;
+  long long first_row;    // global index of row 0 (the generator's counter)
   double R;               // lead-in / lead-out length: 2 x grid diagonal
   const double2* cs;      // [n_angles] (cos, sin) from the host's libm
   const Basis4* basis;    // [K + 1] Hermite basis at s = j / K
@@ -63,7 +64,7 @@ struct SimDev {
 
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon et al., SC'11).  key = (seed, stream),
-// counter = (row, block, 0, 0); uniform = (top 53 bits + 1/2) * 2^-53.
+// counter = (global row, block, 0, 0); uniform = (top 53 bits + 1/2) * 2^-53.
 // ---------------------------------------------------------------------------
 struct U4 {
   unsigned long long w[4];
@@ -262,7 +263,7 @@ __device__ __forceinline__ PathF64 path_setup(const SimDev& S, long long row) {
   double2 cs = S.cs[k];
   double c = cs.x, s = cs.y;
   UniformStream us;
-  us.init((unsigned long long)row, S.seed, S.stream);
+  us.init((unsigned long long)(S.first_row + row), S.seed, S.stream);
   double t = md.t_lo + md.t_span * us.get(0);
   double v = 0.0;
   if (dim == 3) v = md.v_lo + md.v_span * us.get(1);

@@ -3,7 +3,6 @@
 // static device array instead of a caller-provided workspace, for callers
 // that cannot allocate device memory.
 #include <cstdio>
-#include <mutex>
 
 #include "pct_kernels.cuh"
 
@@ -14,10 +13,6 @@ namespace {
 // holds this array until the process exits.
 constexpr long long kStaticTiles = PCT_STATIC_SCAN_MAX_ROWS / pct::kScanTile + 1;
 static __device__ __align__(256) long long g_scan_scratch[kStaticTiles];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-long long* g_scratch_ptr[kMaxDevices] = {};  // device address of g_scan_scratch, per device
 
 }  // namespace
 
@@ -32,28 +27,17 @@ extern "C" pct_status pct_scan_counts_static(int64_t* row_ptr_dev, int64_t n_row
              (long long)n_rows, (long long)PCT_STATIC_SCAN_MAX_ROWS);
     return pct::set_error(PCT_EINVAL, msg);
   }
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) {
-    snprintf(msg, sizeof(msg), "pct_scan_counts_static: cudaGetDevice: %s", cudaGetErrorString(e));
-    return pct::set_error(PCT_ECUDA, msg);
-  }
-  if (dev < 0 || dev >= kMaxDevices) return pct::set_error(PCT_EUNSUPPORTED, "pct_scan_counts_static: device ordinal >= 64");
+  // The array's name is a host-side stand-in; its device address comes from
+  // the runtime, for the calling thread's current device and context.  It is
+  // looked up on every call (no allocation, a table lookup once the module is
+  // loaded), so a cudaDeviceReset or another context on the same device never
+  // leaves a stale address behind.  The first call on a device loads the
+  // module that holds the array.
   long long* scratch = nullptr;
-  {
-    // set-up, once per device, with that device current: the array's name is
-    // a host-side stand-in, its device address comes from the runtime
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-      long long* p = nullptr;
-      e = cudaGetSymbolAddress((void**)&p, g_scan_scratch);
-      if (e != cudaSuccess || !p) {
-        snprintf(msg, sizeof(msg), "pct_scan_counts_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        return pct::set_error(PCT_ECUDA, msg);
-      }
-      g_scratch_ptr[dev] = p;
-    }
-    scratch = g_scratch_ptr[dev];
+  cudaError_t e = cudaGetSymbolAddress((void**)&scratch, g_scan_scratch);
+  if (e != cudaSuccess || !scratch) {
+    snprintf(msg, sizeof(msg), "pct_scan_counts_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    return pct::set_error(PCT_ECUDA, msg);
   }
   // every partial the scan reads is written by the same launch sequence first,
   // so the array needs no clearing between calls

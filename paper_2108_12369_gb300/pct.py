@@ -46,7 +46,7 @@ class PathModel(C.Structure):
 class Geometry(C.Structure):
     _fields_ = [("angles_rad", C.POINTER(C.c_double)), ("n_angles", C.c_int32),
                 ("paths_per_angle", C.c_int64), ("model", PathModel), ("seed", C.c_uint64),
-                ("stream_id", C.c_uint64)]
+                ("stream_id", C.c_uint64), ("first_row", C.c_int64)]
 
 
 class Csr(C.Structure):
@@ -181,7 +181,9 @@ def phantom_rasterize(ph: Phantom, x_true, stream=None):
 
 
 class GeometryArgs:
-    """pct_geometry for a workload dict (keeps the angle array alive)."""
+    """pct_geometry for a workload dict (keeps the angle array alive).  A
+    workload that is a block of angles of a larger acquisition carries the
+    global index of its first row as w["first_row"]."""
 
     def __init__(self, w: dict, stream_id: int = 0):
         self.angles = np.ascontiguousarray(w["angles"], dtype=np.float64)
@@ -193,7 +195,7 @@ class GeometryArgs:
                        m.get("noise_rel", 0.0))
         self.c = Geometry(self.angles.ctypes.data_as(C.POINTER(C.c_double)), len(self.angles),
                           int(w["paths_per_angle"]), pm, C.c_uint64(int(w["seed"])),
-                          C.c_uint64(int(stream_id)))
+                          C.c_uint64(int(stream_id)), int(w.get("first_row", 0)))
         self.n_rows = len(self.angles) * int(w["paths_per_angle"])
 
 

@@ -24,13 +24,14 @@ def angle_shard(n_angles: int, rank: int, world: int):
 
 def shard_workload(w: dict, rank: int, world: int) -> dict:
     """The workload restricted to this rank's angles.  Its local row i is
-    global row row_base() + i of the full acquisition; a rank that must
-    reproduce the full acquisition's protons keys them by the global index
-    (the CPU oracle does; the benchmark's ranks instead draw independent
-    protons with generator stream = rank)."""
+    global row first_row + i of the full acquisition (first_row =
+    row_base()), and the library keys each proton's random numbers by that
+    global index, so the shard's rows are exactly those rows of the whole
+    acquisition."""
     k0, k1 = angle_shard(len(w["angles"]), rank, world)
     s = dict(w)
     s["angles"] = w["angles"][k0:k1]
+    s["first_row"] = int(w.get("first_row", 0)) + k0 * int(w["paths_per_angle"])
     return s
 
 

@@ -108,3 +108,70 @@ def test_fill_host_validates_before_any_device_work(pct):
     st = L.pct_simulate_fill_host(ph.handle, C.byref(geo.c), pct.PREC_MIXED, None, 0, p, p, odd, 1 << 20,
                                   p, p, p, p, None)
     assert st == pct.EINVAL and b"aligned" in L.pct_last_error()
+
+
+class _FakeAllocator:
+    """Allocator callbacks that hand out fake, never-dereferenced addresses and
+    return NULL on call number `fail_at` (1-based); counts every call."""
+
+    def __init__(self, pct, fail_at):
+        self.fail_at, self.calls, self.live, self.freed = fail_at, 0, set(), []
+
+        def alloc(nbytes, ctx):
+            self.calls += 1
+            if self.calls == self.fail_at:
+                return None
+            p = 0x7f0000000000 + 0x1000000 * self.calls
+            self.live.add(p)
+            return p
+
+        def free(p, ctx):
+            self.freed.append(p)
+            self.live.discard(p)
+
+        self.af, self.ff = pct.ALLOC_FN(alloc), pct.FREE_FN(free)
+
+
+@pytest.mark.parametrize("fail_at", [1, 2, 3, 4])
+def test_simulate_allocator_failure_frees_everything(pct, fail_at):
+    """pct_simulate allocates its workspace, x_true, row pointers and b first;
+    when the caller's allocator returns NULL for any of them the call returns
+    PCT_ENOMEM before any device work and frees every block it received."""
+    w = W.neo2_2d_spline(n_angles=3, paths_per_angle=20, n=64, h=3.2)
+    ph, geo = pct.Phantom(w["phantom"]), pct.GeometryArgs(w)
+    fa = _FakeAllocator(pct, fail_at)
+    out = pct.Csr()
+    st = pct.lib().pct_simulate(ph.handle, C.byref(geo.c), pct.PREC_MIXED, fa.af, fa.ff, None, C.byref(out), None)
+    assert st == pct.ENOMEM and "allocator returned NULL" in pct.last_error()
+    assert fa.calls == 4  # the four up-front blocks, nothing after the failure
+    assert not fa.live and len(fa.freed) == 3 and len(set(fa.freed)) == 3
+    assert out.row_ptr is None and out.col is None  # nothing handed out
+
+
+@pytest.mark.parametrize("prec_name", ["mixed", "f64"])
+def test_workspace_one_byte_short_is_refused_before_any_device_work(pct, prec_name):
+    prec = {"mixed": pct.PREC_MIXED, "f64": pct.PREC_F64}[prec_name]
+    w = W.head_3d_spline(n_angles=2, paths_per_angle=30, n=(20, 20, 16), h=(10.0, 10.0, 10.0))
+    ph, geo = pct.Phantom(w["phantom"]), pct.GeometryArgs(w)
+    need = pct.simulate_workspace_size(ph, geo, prec)
+    fake = C.c_void_p(0x7f0000000000)  # never dereferenced: the size check comes first
+    L = pct.lib()
+    st = L.pct_simulate_count(ph.handle, C.byref(geo.c), prec, fake, need - 1, fake, None)
+    assert st == pct.ENOMEM and "smaller than" in pct.last_error()
+    st = L.pct_simulate_fill(ph.handle, C.byref(geo.c), prec, fake, need - 1, fake, fake, fake, fake, fake, None)
+    assert st == pct.ENOMEM
+    pneed = pct.projector_workspace_size(ph, geo, 10, prec)
+    st = L.pct_forward(ph.handle, C.byref(geo.c), None, prec, 0, 10, fake, fake, fake, pneed - 1, None)
+    assert st == pct.ENOMEM
+    st = L.pct_adjoint(ph.handle, C.byref(geo.c), None, prec, 0, 10, fake, fake, fake, pneed - 1, None)
+    assert st == pct.ENOMEM
+
+
+def test_first_row_is_validated(pct):
+    w = W.neo2_2d_spline(n_angles=4, paths_per_angle=10, n=64, h=3.2)
+    ph = pct.Phantom(w["phantom"])
+    assert pct.simulate_workspace_size(ph, pct.GeometryArgs(dict(w, first_row=123456789)), pct.PREC_MIXED) > 0
+    for bad in (-1, (1 << 62) - 39):
+        with pytest.raises(pct.PctError) as e:
+            pct.simulate_workspace_size(ph, pct.GeometryArgs(dict(w, first_row=bad)), pct.PREC_MIXED)
+        assert e.value.status == pct.EINVAL and "first_row" in pct.last_error()

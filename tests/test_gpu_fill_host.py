@@ -67,3 +67,32 @@ def test_host_fill_rejects_staging_smaller_than_a_row(pct):
     for nbytes in (1024, 2 * 1056):  # no room at all; 128 entries per half, rows hold more
         with pytest.raises(pct.PctError):
             host_fill(pct, ph, geo, pct.PREC_MIXED, nbytes)
+
+
+def test_host_fill_rejects_null_entry_buffers_before_any_fill(pct):
+    """With nonzeros to write, a NULL col_host or val_host is refused once the
+    row pointers are read back, before any fill is launched."""
+    import ctypes as C
+    w = W.neo2_2d_spline(n_angles=2, paths_per_angle=50, n=128, h=1.6)
+    ph, geo = pct.Phantom(w["phantom"]), pct.GeometryArgs(w)
+    ws = torch.empty(pct.simulate_workspace_size(ph, geo, pct.PREC_MIXED), dtype=torch.uint8, device="cuda")
+    x = torch.empty(ph.nvox, dtype=torch.float32, device="cuda")
+    rp = torch.empty(geo.n_rows + 1, dtype=torch.int64, device="cuda")
+    pct.phantom_rasterize(ph, x)
+    pct.simulate_count(ph, geo, pct.PREC_MIXED, ws, rp)
+    assert int(rp[-1]) > 0
+    h_rp = torch.empty(geo.n_rows + 1, dtype=torch.int64, pin_memory=True)
+    h = torch.empty(int(rp[-1]), dtype=torch.float32, pin_memory=True)
+    h_b = torch.full((geo.n_rows,), -7.0, dtype=torch.float32, pin_memory=True)
+    staging = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    L = pct.lib()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for col_p, val_p in ((None, h.data_ptr()), (h.data_ptr(), None)):
+        st = L.pct_simulate_fill_host(ph.handle, C.byref(geo.c), pct.PREC_MIXED, C.c_void_p(ws.data_ptr()),
+                                      ws.numel(), C.c_void_p(rp.data_ptr()), C.c_void_p(x.data_ptr()),
+                                      C.c_void_p(staging.data_ptr()), staging.numel(),
+                                      C.c_void_p(h_rp.data_ptr()), C.c_void_p(col_p), C.c_void_p(val_p),
+                                      C.c_void_p(h_b.data_ptr()), stream)
+        assert st == pct.EINVAL and b"NULL col_host or val_host" in L.pct_last_error()
+    torch.cuda.synchronize()
+    assert torch.all(h_b == -7.0)  # nothing was filled

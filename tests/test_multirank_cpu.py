@@ -1,7 +1,10 @@
 """The multi-GPU host logic with two gloo ranks on CPU: angle-block shards
 reassemble the single-process CSR exactly (through the all-gathered nonzero
 offsets), the summed shard adjoints equal the full A^T r, and timings reduce
-to the maximum.  The per-shard rows come from the CPU oracle."""
+to the maximum.  The per-shard rows come from the CPU oracle; each rank also
+builds the library's geometry of its block (global first row) and has the
+library accept it on the host.  The GPU side of the same partition (blocks
+concatenating into the whole CSR bit for bit) is tests/test_gpu_shards.py."""
 import os
 import socket
 
@@ -35,6 +38,15 @@ def _worker(rank, world, port, out_dir):
         x = ph.raster().astype(np.float32)
         sim = O.Simulation(ph, x, w["angles"], w["paths_per_angle"], w["model"], w["seed"])
         rp, col, val, bc, bn = sim.rows(rows)
+        # the library's view of this rank's block: its geometry carries the
+        # global first row, which keys the block's random numbers
+        from paper_2108_12369_gb300 import pct as P
+        sw = shard.shard_workload(w, rank, world)
+        geo = P.GeometryArgs(sw)
+        assert geo.c.first_row == rows[0] and geo.n_rows == len(rows)
+        assert list(geo.angles) == list(w["angles"][shard.angle_shard(7, rank, world)[0]:][:len(sw["angles"])])
+        ph_lib = P.Phantom(w["phantom"])
+        assert P.simulate_workspace_size(ph_lib, geo, P.PREC_MIXED) > 0  # accepted on the host
         off, total = shard.nnz_offsets(int(rp[-1]))
         # the shard's adjoint contribution
         A = sp.csr_matrix((val, col, rp), shape=(len(rows), ph.nvox))
@@ -49,6 +61,8 @@ def _worker(rank, world, port, out_dir):
 
 
 def test_two_rank_shards_reassemble_the_full_system(tmp_path):
+    from paper_2108_12369_gb300 import build
+    build.build()  # the ranks load the library's host side
     world = 2
     mp.spawn(_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
     parts = [np.load(tmp_path / f"r{k}.npz") for k in range(world)]

@@ -468,6 +468,145 @@ def test_mcs_exit_draws_are_bivariate_normal(orc):
     assert abs(np.corrcoef(lats, angs)[0, 1] - rho) < 4 * (1 - rho * rho) / math.sqrt(n)
 
 
+def _independent_pairs(seed, stream, row, n_pairs):
+    """The first n_pairs polar-method pairs of proton `row` (uniforms from 4 on),
+    from numpy's Philox words and libm's log: independent of the oracle."""
+    out, j, blocks = [], 4, {}
+
+    def u(k):
+        b = k >> 2
+        if b not in blocks:
+            blocks[b] = _numpy_block([seed, stream], row, b)
+        return (float(int(blocks[b][k & 3]) >> 11) + 0.5) * 2.0**-53
+
+    while len(out) < n_pairs:
+        v1, v2 = 2 * u(j) - 1, 2 * u(j + 1) - 1
+        j += 2
+        s = v1 * v1 + v2 * v2
+        if 0 < s < 1:
+            f = math.sqrt(-2 * math.log(s) / s)
+            out.append((v1 * f, v2 * f))
+    return out
+
+
+def _far_hull_point(P0, g, hull, dim):
+    """Far intersection of the line P0 + mu g with the hull (closed form)."""
+    a = np.array(hull["a"][:dim])
+    c = np.array(hull["c"][:dim])
+    e, f = g[:dim] / a, (P0[:dim] - c) / a
+    A2, B1, C0 = e @ e, e @ f, f @ f - 1
+    return P0 + (-B1 + math.sqrt(B1 * B1 - A2 * C0)) / A2 * g
+
+
+def _mcs_3d_sim(orc, P, rho, sig=(1.0, 0.02, 0.015)):
+    w = W.head_3d_spline(n_angles=6, paths_per_angle=P, n=(100, 100, 80), h=(2.0, 2.0, 2.0))
+    m = dict(w["model"])
+    m.update(model=W.STRAIGHT_MCS, sigma_lat=sig[0], sigma_in=sig[1], sigma_out=sig[2], rho=rho)
+    ph = orc.Phantom(w["phantom"])
+    sim = orc.Simulation(ph, ph.raster().astype(np.float32), w["angles"], P, m, w["seed"])
+    R = 2 * math.sqrt(200.0 ** 2 + 200.0 ** 2 + 160.0 ** 2)
+    return sim, w, R
+
+
+def _mcs_3d_recover(V, th, R, hull):
+    """Entry slopes (t, v) and exit pairs in the ut- and uv-planes of a 3D
+    STRAIGHT_MCS path V = [P0 - R g0, P0, P1, P1 + R g1] (Sec. II-B)."""
+    t = np.array([-math.sin(th), math.cos(th), 0.0])
+    v = np.array([0.0, 0.0, 1.0])
+    g0 = (V[1] - V[0]) / R
+    g1 = (V[3] - V[2]) / R
+    n_t = np.array([-g0[1], g0[0], 0.0])
+    n_v = np.cross(g0, n_t)
+    Q1 = _far_hull_point(V[1], g0, hull, 3)
+    d, dg = V[2] - Q1, g1 - g0
+    return {"in_t": float(g0 @ t), "in_v": float(g0 @ v),
+            "lat_t": float(d @ n_t / (n_t @ n_t)), "lat_v": float(d @ n_v / (n_v @ n_v)),
+            "ang_t": float(dg @ n_t / (n_t @ n_t)), "ang_v": float(dg @ n_v / (n_v @ n_v))}
+
+
+def test_mcs_3d_draws_equal_independent_draws(orc):
+    """Every draw of a 3D MCS proton, recovered from its path geometry, equals
+    the same draw recomputed outside the oracle: exit (displacement, slope) in
+    the ut-plane from pair 1, in the uv-plane (along n_v = g0 x n_t) from pair
+    2, entry slopes along t and v from pair 3 (Sec. II-B, bivariate normal)."""
+    sig_lat, sig_in, sig_out, rho = 1.0, 0.02, 0.015, 0.4
+    sim, w, R = _mcs_3d_sim(orc, 40, rho, (sig_lat, sig_in, sig_out))
+    hull = w["phantom"]["regions"][0]
+    rc = math.sqrt(1 - rho * rho)
+    checked = 0
+    for row in range(sim.n_rows):
+        V = sim.path(row)
+        (a1, a2), (b1, b2), (c1, c2) = _independent_pairs(w["seed"], 0, row, 3)
+        th = w["angles"][row // 40]
+        if len(V) == 2:  # missed the hull: only the entry slopes shape the line
+            g0 = (V[1] - V[0]) / (2 * R)
+            assert abs(g0 @ np.array([-math.sin(th), math.cos(th), 0]) - sig_in * c1) < 1e-12
+            assert abs(g0[2] - sig_in * c2) < 1e-12
+            continue
+        got = _mcs_3d_recover(V, th, R, hull)
+        want = {"lat_t": sig_lat * a1, "ang_t": sig_out * (rho * a1 + rc * a2),
+                "lat_v": sig_lat * b1, "ang_v": sig_out * (rho * b1 + rc * b2),
+                "in_t": sig_in * c1, "in_v": sig_in * c2}
+        for k in want:
+            tol = 1e-9 if k.startswith("lat") else 1e-11
+            assert abs(got[k] - want[k]) < tol, (row, k, got[k], want[k])
+        checked += 1
+    assert checked > 150
+
+
+def test_mcs_3d_exit_pairs_and_entry_slopes_statistics(orc):
+    """The 3D draws have the requested sigmas, the correlation rho within each
+    plane, none across planes, and independent entry slopes (Sec. II-B: MCS in
+    the ut- and uv-planes)."""
+    sig_lat, sig_in, sig_out, rho = 1.5, 0.02, 0.01, -0.5
+    P = 1600
+    sim, w, R = _mcs_3d_sim(orc, P, rho, (sig_lat, sig_in, sig_out))
+    hull = w["phantom"]["regions"][0]
+    rec = []
+    for row in range(sim.n_rows):
+        V = sim.path(row)
+        if len(V) == 4:
+            rec.append(_mcs_3d_recover(V, w["angles"][row // P], R, hull))
+    n = len(rec)
+    assert n > 5000
+    col = {k: np.array([r[k] for r in rec]) for k in rec[0]}
+    for k, s in (("lat_t", sig_lat), ("lat_v", sig_lat), ("ang_t", sig_out), ("ang_v", sig_out),
+                 ("in_t", sig_in), ("in_v", sig_in)):
+        assert abs(col[k].mean()) < 4 * s / math.sqrt(n), k
+        assert abs(col[k].std() - s) < 4 * s / math.sqrt(2 * n), k
+    tol = 4 * (1 - rho * rho) / math.sqrt(n)
+    assert abs(np.corrcoef(col["lat_t"], col["ang_t"])[0, 1] - rho) < tol
+    assert abs(np.corrcoef(col["lat_v"], col["ang_v"])[0, 1] - rho) < tol
+    for a, b in (("lat_t", "lat_v"), ("ang_t", "ang_v"), ("lat_t", "ang_v"), ("in_t", "in_v"),
+                 ("in_t", "lat_t"), ("in_v", "lat_v")):
+        assert abs(np.corrcoef(col[a], col[b])[0, 1]) < 4 / math.sqrt(n), (a, b)
+
+
+def test_entry_slopes_2d_statistics(orc):
+    """2D: the entry slope recovered from the incoming line against u has
+    sigma_in (the MCS statistics tests above it set sigma_in = 0)."""
+    sig_in = 0.03
+    w = W.neo2_2d_spline(n_angles=4, paths_per_angle=2500)
+    m = dict(w["model"])
+    m.update(model=W.STRAIGHT_MCS, sigma_in=sig_in)
+    ph = orc.Phantom(w["phantom"])
+    sim = orc.Simulation(ph, ph.raster().astype(np.float32), w["angles"], 2500, m, w["seed"])
+    R = 2 * math.hypot(204.8, 204.8)
+    sl = []
+    for row in range(sim.n_rows):
+        V = sim.path(row)[:, :2]
+        th = w["angles"][row // 2500]
+        u = np.array([math.cos(th), math.sin(th)])
+        t = np.array([-math.sin(th), math.cos(th)])
+        g0 = (V[1] - V[0]) / (R if len(V) == 4 else 2 * R)
+        assert abs(g0 @ u - 1) < 1e-12  # g0 = u + slope t, not normalised
+        sl.append(float(g0 @ t))
+    sl = np.array(sl)
+    n = len(sl)
+    assert abs(sl.mean()) < 4 * sig_in / math.sqrt(n)
+    assert abs(sl.std() - sig_in) < 4 * sig_in / math.sqrt(2 * n)
+
+
 # --------------------------------------------------------------------------
 # WEPL (Sec. II-C: b_i = <a_i, x_true>, optional noise)
 # --------------------------------------------------------------------------
