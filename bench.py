@@ -9,12 +9,20 @@ Metric: proton paths per second (whole job), with the CSR bytes per second
 and the fill kernel's achieved HBM bandwidth against the measured peak.
 
   python bench.py [--gpus N --steps K --warmup W] [--precision mixed|f64]
-                  [--impl ours|reference] [--workload neo2_2d_spline]
+                  [--impl ours|reference] [--workload head_3d_spline]
 
-Under torchrun (N > 1) every rank simulates its own independent batch of
-protons (generator stream = rank): weak scaling, no collective on the data
-path.  `--impl reference` times the CPU oracle on a bounded sample of the
-same workload (rank 0 only).
+The default workload is the 3D head: 200x200x160 voxels of 1 mm, 90 angles x
+200,000 cubic-spline paths with MCS draws, 1 % WEPL noise (18M rows).  After
+the timed loop the line also carries the all-FP64 form's step time on the
+same workload (the mixed form's speedup) and the max / RMS errors of A and b
+against the CPU oracle on a row sample, for both forms.
+
+Under torchrun (N > 1) the ranks split one acquisition into contiguous angle
+blocks (Sec. IV), each block keyed by its global first row so that the blocks
+are exactly the rows of the single-GPU run: strong scaling, no collective on
+the data path (one all-gather of the blocks' nonzero counts places them in
+the global CSR).  `--impl reference` times the CPU oracle on a bounded sample
+of the same workload (rank 0 only).
 """
 from __future__ import annotations
 
@@ -205,11 +213,48 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def accuracy(w, rows, rp_dev, col_dev, val_dev, b_dev, x_max, threads):
+    """Max / RMS error of A's values and of b against the oracle on the given
+    global rows (the comparison rule of the parity tests): indices must match
+    exactly, value errors relative to the row sum, b errors relative to
+    max(|b|, row sum x max RSP).  rp_dev etc. hold the rows first_row + i."""
+    import torch
+    from oracle import oracle as O
+    first = int(w.get("first_row", 0))
+    loc = torch.as_tensor(rows - first, dtype=torch.int64, device=rp_dev.device)
+    r0, r1 = rp_dev[loc], rp_dev[loc + 1]
+    lens = (r1 - r0).cpu().numpy()
+    idx = torch.repeat_interleave(r0, r1 - r0) + (
+        torch.arange(int(lens.sum()), device=rp_dev.device) -
+        torch.repeat_interleave(torch.cumsum(r1 - r0, 0) - (r1 - r0), r1 - r0))
+    col_g = col_dev[idx].cpu().numpy()
+    val_g = val_dev[idx].cpu().numpy().astype(np.float64)
+    b_g = b_dev[loc].cpu().numpy().astype(np.float64)
+    ph = O.Phantom(w["phantom"])
+    x = ph.raster().astype(np.float32)
+    full_angles = w.get("all_angles", w["angles"])
+    sim = O.Simulation(ph, x, full_angles, w["paths_per_angle"], w["model"], w["seed"])
+    rp_o, col_o, val_o, _, b_o = sim.rows(rows, threads=threads)
+    ok_idx = bool(np.array_equal(np.diff(rp_o), lens) and np.array_equal(col_o, col_g))
+    out = {"rows": int(len(rows)), "nnz": int(len(col_o)), "indices_exact": ok_idx}
+    if ok_idx and len(col_o):
+        rid = np.repeat(np.arange(len(rows)), np.diff(rp_o))
+        rowsum = np.bincount(rid, weights=val_o, minlength=len(rows))
+        aerr = np.abs(val_g - val_o)
+        berr = np.abs(b_g - b_o)
+        scale = np.maximum(np.abs(b_o), rowsum * float(x_max))
+        out.update(val_max_rel=float((aerr / np.maximum(rowsum[rid], 1e-30)).max()),
+                   val_rms_abs=float(np.sqrt(np.mean(aerr ** 2))), val_max_abs=float(aerr.max()),
+                   b_max_rel=float((berr / np.maximum(scale, 1e-30)).max()),
+                   b_rms_abs=float(np.sqrt(np.mean(berr ** 2))))
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2108_12369_gb300 import build as B, pct
+    from paper_2108_12369_gb300 import build as B, pct, shard
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -225,36 +270,43 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     prec = {"mixed": pct.PREC_MIXED, "f64": pct.PREC_F64}[args.precision]
-    w = workload(args.workload, args.angles, args.paths_per_angle)
+    w_all = workload(args.workload, args.angles, args.paths_per_angle)
+    # one acquisition split into contiguous angle blocks, one per rank (Sec. IV)
+    w = shard.shard_workload(w_all, rank, world)
+    w["all_angles"] = w_all["angles"]
     ph = pct.Phantom(w["phantom"])
-    geo = pct.GeometryArgs(w, stream_id=rank)
+    geo = pct.GeometryArgs(w)
     n_rows = geo.n_rows
+    total_rows = W.n_rows(w_all)
     ws = torch.empty(pct.simulate_workspace_size(ph, geo, prec), dtype=torch.uint8, device=dev)
     x = torch.empty(ph.nvox, dtype=torch.float32, device=dev)
     rp = torch.empty(n_rows + 1, dtype=torch.int64, device=dev)
-    b = torch.empty(n_rows, dtype=torch.float32, device=dev)
+    b = torch.empty(max(n_rows, 1), dtype=torch.float32, device=dev)
     pct.phantom_rasterize(ph, x)
     pct.simulate_count(ph, geo, prec, ws, rp)
     nnz = int(rp[-1].item())
-    col = torch.empty(nnz, dtype=torch.int32, device=dev)
-    val = torch.empty(nnz, dtype=torch.float32, device=dev)
+    col = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+    val = torch.empty(max(nnz, 1), dtype=torch.float32, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(ev=None):
-        if ev:
-            ev[0].record(stream)
-        pct.phantom_rasterize(ph, x)
-        pct.simulate_count(ph, geo, prec, ws, rp)
-        n = int(rp[-1].item())  # nnz read-back sizes the fill, as a caller must
-        if n != nnz:
-            raise RuntimeError("nnz changed between steps")
-        if ev:
-            ev[1].record(stream)
-        pct.simulate_fill(ph, geo, prec, ws, rp, x, col, val, b)
-        if ev:
-            ev[2].record(stream)
+    def make_step(p, wsp):
+        def step(ev=None):
+            if ev:
+                ev[0].record(stream)
+            pct.phantom_rasterize(ph, x)
+            pct.simulate_count(ph, geo, p, wsp, rp)
+            n = int(rp[-1].item())  # nnz read-back sizes the fill, as a caller must
+            if n != nnz:
+                raise RuntimeError("nnz changed between steps")
+            if ev:
+                ev[1].record(stream)
+            pct.simulate_fill(ph, geo, p, wsp, rp, x, col, val, b)
+            if ev:
+                ev[2].record(stream)
+        return step
 
+    step = make_step(prec, ws)
     for _ in range(args.warmup):
         step()
         flush.zero_()
@@ -277,11 +329,45 @@ def run_ours(args):
     step_ms = [e[0].elapsed_time(e[2]) for e in evs]
     fill_ms = [e[1].elapsed_time(e[2]) for e in evs]
     total_s = sum(step_ms) / 1e3
+    nz_off, nnz_total = 0, nnz
     if world > 1:
         t = torch.tensor([total_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_s = float(t.item())
-    value = world * n_rows * args.steps / total_s
+        nz_off, nnz_total = shard.nnz_offsets(nnz)  # the blocks' places in the global CSR
+    value = total_rows * args.steps / total_s
+
+    # accuracy of this form against the oracle on an even stride sample of
+    # this rank's rows (after the timed loop)
+    x_max = float(x.max().item())
+    sample = None
+    acc = {}
+    if rank == 0 and args.accuracy_rows > 0 and n_rows > 0:
+        first = int(w["first_row"])
+        sample = first + np.unique(np.linspace(0, n_rows - 1, min(args.accuracy_rows, n_rows)).astype(np.int64))
+        acc[args.precision] = accuracy(w, sample, rp, col, val, b, x_max, os.cpu_count() or 1)
+
+    # the other arithmetic form on the same workload, same buffers: the mixed
+    # form's speedup over the all-FP64 form at the accuracy reported
+    other = None
+    if rank == 0 and world == 1 and args.fp64_steps > 0 and args.precision == "mixed":
+        ws64 = torch.empty(pct.simulate_workspace_size(ph, geo, pct.PREC_F64), dtype=torch.uint8, device=dev)
+        step64 = make_step(pct.PREC_F64, ws64)
+        step64()
+        flush.zero_()
+        torch.cuda.synchronize()
+        ev64 = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.fp64_steps)]
+        for s in range(args.fp64_steps):
+            step64(ev64[s])
+            flush.zero_()
+        torch.cuda.synchronize()
+        ms64 = statistics.mean(e[0].elapsed_time(e[2]) for e in ev64)
+        other = {"fp64_ms_per_step": ms64, "mixed_ms_per_step": 1e3 * total_s / args.steps,
+                 "mixed_speedup": ms64 / (1e3 * total_s / args.steps), "fp64_steps": args.fp64_steps,
+                 "fp64_fill_ms": statistics.mean(e[1].elapsed_time(e[2]) for e in ev64)}
+        if sample is not None:
+            acc["f64"] = accuracy(w, sample, rp, col, val, b, x_max, os.cpu_count() or 1)
+        del ws64
 
     # end to end through the C ABI with host buffers: angle / basis tables go
     # up from host memory inside every call; pct_simulate_fill_host writes
@@ -291,9 +377,9 @@ def run_ours(args):
     small = args.no_e2e
     del col, val  # the host path needs no device CSR
     h_rp = torch.empty(1 if small else n_rows + 1, dtype=torch.int64, pin_memory=True)
-    h_col = torch.empty(1 if small else nnz, dtype=torch.int32, pin_memory=True)
-    h_val = torch.empty(1 if small else nnz, dtype=torch.float32, pin_memory=True)
-    h_b = torch.empty(1 if small else n_rows, dtype=torch.float32, pin_memory=True)
+    h_col = torch.empty(1 if small else max(nnz, 1), dtype=torch.int32, pin_memory=True)
+    h_val = torch.empty(1 if small else max(nnz, 1), dtype=torch.float32, pin_memory=True)
+    h_b = torch.empty(1 if small else max(n_rows, 1), dtype=torch.float32, pin_memory=True)
     staging = torch.empty(256 if small else 1 << 30, dtype=torch.uint8, device=dev)
     e2e_steps = 0 if small else max(1, min(args.steps, 3))
 
@@ -308,6 +394,8 @@ def run_ours(args):
         step_host()  # warm-up (first launches, first writes to the pinned pages), untimed
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     e0.record(stream)
     for _ in range(e2e_steps):
         step_host()
@@ -318,7 +406,7 @@ def run_ours(args):
         t = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e_value = world * n_rows * e2e_steps / e2e_s if e2e_steps else None
+    e2e_value = total_rows * e2e_steps / e2e_s if e2e_steps else None
     K = w["model"].get("spline_segments", 1)
     h2d = len(w["angles"]) * 16 + (K + 1) * 32
     d2h = (n_rows + 1) * 8 + nnz * 8 + n_rows * 4
@@ -335,18 +423,20 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "mixed" else "f64", "precision": args.precision,
         "data": "synthetic",
         "config": {"workload": w["name"], "grid": list(w["phantom"]["n"][:w["phantom"]["dim"]]),
-                   "voxel_mm": w["phantom"]["h"][0], "angles": len(w["angles"]),
-                   "paths_per_angle": w["paths_per_angle"], "rows_per_gpu": n_rows, "nnz_per_gpu": nnz,
+                   "voxel_mm": w["phantom"]["h"][0], "angles": len(w_all["angles"]),
+                   "paths_per_angle": w["paths_per_angle"], "rows": total_rows, "rows_rank0": n_rows,
+                   "nnz": nnz_total, "nnz_rank0": nnz,
                    "path_model": "spline" if w["model"]["model"] == W.SPLINE else "straight",
                    "spline_segments": K, "noise_rel": w["model"].get("noise_rel", 0.0),
                    "l2": "512 MB write between steps (untimed); outputs per step >> L2",
-                   "parallelism": f"independent protons per GPU x{world}"},
-        "csr_gbs": (8.0 * nnz + 12.0 * n_rows) * world * args.steps / total_s / 1e9,
-        "nnz_per_s": world * nnz * args.steps / total_s,
+                   "parallelism": (f"angle blocks of one acquisition over {world} GPUs (global row bases)"
+                                   if world > 1 else "one GPU")},
+        "csr_gbs": (8.0 * nnz_total + 12.0 * total_rows) * args.steps / total_s / 1e9,
+        "nnz_per_s": nnz_total * args.steps / total_s,
         "roofline": {"bound": "hbm", "kernel": FILL_KERNEL[args.precision], "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": f"{peak_kind} hbm_gbs (copy, burst)",
@@ -360,8 +450,12 @@ def run_ours(args):
                 "steps": e2e_steps},
         "gpu_launches": LAUNCHES_PER_STEP[args.precision] * args.steps,
     }
+    if other is not None:
+        line["mixed_vs_f64"] = other
+    if acc:
+        line["accuracy_vs_oracle"] = acc
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(w_all, args.cpu_seconds)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -489,7 +583,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "f64"], default="mixed")
-    ap.add_argument("--workload", default="neo2_2d_spline")
+    ap.add_argument("--workload", default="head_3d_spline")
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the all-FP64 form (0: skip)")
+    ap.add_argument("--accuracy-rows", type=int, default=2000,
+                    help="rows sampled for the error statistics against the oracle (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--reference-rows", type=int, default=60000)

@@ -309,6 +309,26 @@ pct_status pct_batch_destroy(pct_batch* batch);
 #define PCT_STATIC_SCAN_MAX_ROWS (1LL << 28)
 pct_status pct_scan_counts_static(int64_t* row_ptr_dev, int64_t n_rows, void* stream);
 
+/* ---- reconstruction: string-averaging projections (Sec. II-D) ----------
+ * The paper's reconstruction algorithm (SAP, Censor et al.) on an explicit
+ * CSR A and b, for checking the simulated systems.  The rows are split into
+ * n_strings strings M, string t holding rows t, t + M, t + 2M, ... in
+ * increasing order.  One iteration: every string starts from x and projects
+ * its rows in order,
+ *   y <- y + lambda (b_i - <a_i, y>) / ||a_i||^2 a_i   (rows with a_i = 0 skipped),
+ * then x <- sum_t w_t y_t with w_t = weights[t] (host array of M doubles,
+ * finite, summing to 1 within 1e-9) or 1 / M for weights = NULL.  (The
+ * paper's printed update uses <a_i, x_k> and the opposite sign; this is the
+ * projection of SAP as Censor et al. define it.)  FP32 iterates and sums,
+ * FP64 averaging; summation order within a row is not fixed.  x_dev holds the
+ * start on entry and the result on completion (in stream order); b_dev is
+ * float [A->n_rows].  Workspace: pct_sap_workspace_size bytes (M copies of
+ * x), caller-owned.  EINVAL on bad sizes, lambda not finite, weights not
+ * summing to 1; ENOMEM when the workspace is too small. */
+pct_status pct_sap_workspace_size(int64_t n_cols, int32_t n_strings, size_t* bytes);
+pct_status pct_sap(const pct_csr* A, const float* b_dev, int32_t n_strings, const double* weights, double lambda,
+                   int32_t iterations, float* x_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
+
 /* message of the calling thread's last failure ("" if none) */
 const char* pct_last_error(void);
 

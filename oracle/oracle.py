@@ -94,6 +94,9 @@ def lib():
         _lib.orc_fill_rows.argtypes = [P(_Sim), P(C.c_int64), C.c_int64, P(C.c_int64),
                                        P(C.c_int32), P(C.c_double), P(C.c_double), P(C.c_double),
                                        C.c_int32]
+        _lib.orc_sap.argtypes = [C.c_int64, C.c_int64, P(C.c_int64), P(C.c_int32), P(C.c_double),
+                                 P(C.c_double), C.c_int32, P(C.c_double), C.c_double, C.c_int32,
+                                 P(C.c_double)]
     return _lib
 
 
@@ -240,3 +243,19 @@ def simulate(desc: dict, angles, paths_per_angle: int, model: dict, seed: int, r
     sim = Simulation(ph, x, angles, paths_per_angle, model, seed, stream)
     rp, cols, vals, bc, bn = sim.rows(rows, threads)
     return {"x_true": x, "row_ptr": rp, "col": cols, "val": vals, "b_clean": bc, "b": bn}
+
+
+def sap(row_ptr, col, val, b, n_cols: int, n_strings: int, lam: float, iterations: int, x0=None,
+        weights=None) -> np.ndarray:
+    """String-averaging projections (Sec. II-D) in FP64: `iterations` sweeps
+    from x0 (default 0); string t = rows t, t + M, ...; returns x."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    c = np.ascontiguousarray(col, dtype=np.int32)
+    v = np.ascontiguousarray(val, dtype=np.float64)
+    bb = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n_cols, np.float64) if x0 is None else np.array(x0, dtype=np.float64)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    lib().orc_sap(len(rp) - 1, n_cols, _ptr(rp, C.c_int64), _ptr(c, C.c_int32), _ptr(v, C.c_double),
+                  _ptr(bb, C.c_double), int(n_strings), None if w is None else _ptr(w, C.c_double),
+                  float(lam), int(iterations), _ptr(x, C.c_double))
+    return x

@@ -586,3 +586,41 @@ void orc_fill_rows(const orc_sim* sim, const int64_t* rows, int64_t n, const int
     if (b_noisy) b_noisy[q] = bn;
   }
 }
+
+/* ------------------------------------------------------------------------- */
+/* Reconstruction: string-averaging projections (Sec. II-D, SAP)             */
+/*                                                                           */
+/* The paper's update reads <a^i, x_k> and adds lambda (<a^i, x_k> - b_i);   */
+/* here the projection of the current string iterate y onto row i's         */
+/* hyperplane is taken: y + lambda (b_i - <a_i, y>) / ||a_i||^2 a_i (Censor's */
+/* SAP; with lambda = 1 the new y satisfies row i exactly).  Each string     */
+/* starts from x; x becomes the weighted average of the string ends.         */
+/* ------------------------------------------------------------------------- */
+void orc_sap(int64_t n_rows, int64_t n_cols, const int64_t* row_ptr, const int32_t* col,
+             const double* val, const double* b, int32_t M, const double* w, double lambda,
+             int32_t iterations, double* x) {
+  if (M < 1 || n_cols < 1) return;
+  double* y = (double*)malloc(sizeof(double) * (size_t)n_cols);
+  double* acc = (double*)malloc(sizeof(double) * (size_t)n_cols);
+  for (int32_t it = 0; it < iterations; ++it) {
+    for (int64_t j = 0; j < n_cols; ++j) acc[j] = 0.0;
+    for (int32_t t = 0; t < M; ++t) {
+      for (int64_t j = 0; j < n_cols; ++j) y[j] = x[j];
+      for (int64_t i = t; i < n_rows; i += M) {
+        double dot = 0.0, nrm = 0.0;
+        for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+          dot = dot + val[q] * y[col[q]];
+          nrm = nrm + val[q] * val[q];
+        }
+        if (!(nrm > 0.0)) continue;
+        double c = lambda * (b[i] - dot) / nrm;
+        for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) y[col[q]] = y[col[q]] + c * val[q];
+      }
+      double wt = w ? w[t] : 1.0 / (double)M;
+      for (int64_t j = 0; j < n_cols; ++j) acc[j] = acc[j] + wt * y[j];
+    }
+    for (int64_t j = 0; j < n_cols; ++j) x[j] = acc[j];
+  }
+  free(y);
+  free(acc);
+}

@@ -17,6 +17,7 @@
  *     intersecting the path with the voxel planes      (Sec. II-C, Mathematical
  *     Formulation; the Ax=b statement of Sec. II)
  *   - b_i = <a_i, x_true> (+ relative Gaussian noise)   (Sec. II-C)
+ *   - x from A, b by string-averaging projections        (Sec. II-D, SAP)
  * All floating point is IEEE binary64, compiled with -ffp-contract=off;
  * every fused multiply-add is an explicit fma() call.
  */
@@ -106,6 +107,16 @@ void orc_count_rows(const orc_sim* sim, const int64_t* rows, int64_t n, int64_t*
 void orc_fill_rows(const orc_sim* sim, const int64_t* rows, int64_t n, const int64_t* off,
                    int32_t* cols, double* vals, double* b_clean, double* b_noisy,
                    int32_t threads);
+
+/* String-averaging projections (Sec. II-D, SAP; Censor et al.), the paper's
+   reconstruction algorithm, in FP64.  Rows are partitioned into M strings,
+   string t holding rows t, t + M, t + 2M, ... in increasing order.  One
+   iteration: for every string, y = x, then for each of its rows i in order
+     y <- y + lambda (b_i - <a_i, y>) / ||a_i||^2 a_i   (rows with a_i = 0 skipped);
+   then x <- sum_t w_t y_t (w = NULL: w_t = 1 / M).  In place on x[n_cols]. */
+void orc_sap(int64_t n_rows, int64_t n_cols, const int64_t* row_ptr, const int32_t* col,
+             const double* val, const double* b, int32_t M, const double* w, double lambda,
+             int32_t iterations, double* x);
 
 #ifdef __cplusplus
 }

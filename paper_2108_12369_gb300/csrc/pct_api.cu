@@ -846,6 +846,45 @@ extern "C" pct_status pct_batch_params(const pct_batch* b, int32_t* grid_mult, i
   return PCT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// reconstruction (Sec. II-D)
+// ---------------------------------------------------------------------------
+extern "C" pct_status pct_sap_workspace_size(int64_t n_cols, int32_t n_strings, size_t* bytes) {
+  if (!bytes || n_cols < 0 || n_strings < 1 || n_strings > (1 << 24))
+    return fail(PCT_EINVAL, "pct_sap_workspace_size: bad arguments");
+  *bytes = sap_workspace_bytes(n_cols, n_strings);
+  return PCT_OK;
+}
+
+extern "C" pct_status pct_sap(const pct_csr* A, const float* b, int32_t M, const double* weights, double lambda,
+                              int32_t iterations, float* x, void* ws, size_t ws_bytes, void* stream) {
+  if (!A || !x) return fail(PCT_EINVAL, "pct_sap: NULL A or x");
+  if (A->n_rows < 0 || A->n_cols < 1 || A->n_cols >= (1LL << 31)) return fail(PCT_EINVAL, "pct_sap: bad A sizes");
+  if (A->n_rows > 0 && (!A->row_ptr || !A->col || !A->val || !b)) return fail(PCT_EINVAL, "pct_sap: incomplete CSR or b");
+  if (M < 1 || M > (1 << 24)) return fail(PCT_EINVAL, "pct_sap: n_strings = %d outside 1..2^24", M);
+  if (iterations < 0) return fail(PCT_EINVAL, "pct_sap: negative iteration count");
+  if (!std::isfinite(lambda)) return fail(PCT_EINVAL, "pct_sap: lambda must be finite");
+  std::vector<double> w((size_t)M, 1.0 / (double)M);
+  if (weights) {
+    double s = 0.0;
+    for (int t = 0; t < M; ++t) {
+      if (!std::isfinite(weights[t])) return fail(PCT_EINVAL, "pct_sap: weight %d is not finite", t);
+      w[t] = weights[t];
+      s += weights[t];
+    }
+    if (std::fabs(s - 1.0) > 1e-9) return fail(PCT_EINVAL, "pct_sap: weights sum to %.17g, not 1", s);
+  }
+  const size_t need = sap_workspace_bytes(A->n_cols, M);
+  if (!ws || ws_bytes < need) return fail(PCT_ENOMEM, "pct_sap: workspace of %zu bytes is smaller than %zu", ws_bytes, need);
+  cudaStream_t st = (cudaStream_t)stream;
+  // pageable source: the copy returns once the weights are staged
+  if (cudaMemcpyAsync(ws, w.data(), sizeof(double) * (size_t)M, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return cuda_check("pct_sap: weights");
+  launch_sap((const long long*)A->row_ptr, A->col, A->val, b, A->n_rows, A->n_cols, M, (const double*)ws,
+             (float)lambda, iterations, x, ws, st);
+  return cuda_check("pct_sap launch");
+}
+
 extern "C" const char* pct_last_error(void) { return g_err.c_str(); }
 
 pct_status pct::set_error(pct_status st, const char* msg) {

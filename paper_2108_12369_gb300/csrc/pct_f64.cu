@@ -1,6 +1,6 @@
-// pct_f64.cu -- all-FP64 form of the simulation kernels: NEO raster
-// (Sec. II-A), per-proton path + traversal count and fill (Sec. II-B, II-C),
-// the row-pointer scan, and CSR / matrix-free projectors (Ax, A^T r).
+// pct_f64.cu -- all-FP64 form of the simulation kernels: per-proton path +
+// traversal count and fill (Sec. II-B, II-C) and the matrix-free projectors
+// (Ax, A^T r).
 //
 // One thread per proton; every floating-point step is the FP64 definition.
 // This is the comparison form for PCT_PREC_MIXED and the exact fallback's
@@ -9,62 +9,6 @@
 #include "pct_kernels.cuh"
 
 namespace pct {
-
-// ---------------------------------------------------------------------------
-// Raster (Sec. II-A): centre point, or mean over the 2^dim corners.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double rsp_at(const PhantomDev& ph, const double p[3]) {
-  int axes = (ph.g.dim == 3 && ph.kind == PCT_ELLIPSOID) ? 3 : 2;
-  double v = 0.0;
-  for (int r = 0; r < ph.n_regions; ++r) {
-    double q = 0.0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      if (a >= axes) break;
-      double d = (p[a] - ph.c[r][a]) / ph.a[r][a];
-      q = q + d * d;
-    }
-    if (q <= 1.0) v = ph.rsp[r];
-  }
-  return v;
-}
-
-__global__ void k_raster(PhantomDev ph, float* __restrict__ x, long long nvox) {
-  long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (j >= nvox) return;
-  const GridDev& g = ph.g;
-  int idx[3];
-  idx[0] = (int)(j % g.n[0]);
-  long long r = j / g.n[0];
-  idx[1] = (int)(r % g.n[1]);
-  idx[2] = (g.dim == 3) ? (int)(r / g.n[1]) : 0;
-  double p[3] = {0.0, 0.0, 0.0};
-  double val;
-  if (ph.raster == PCT_RASTER_CENTER) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-      if (a < g.dim) p[a] = g.o[a] + ((double)idx[a] + 0.5) * g.h[a];
-    val = rsp_at(ph, p);
-  } else {
-    int nc = (g.dim == 3) ? 8 : 4;
-    double sum = 0.0;
-    for (int c = 0; c < nc; ++c) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-        if (a < g.dim) p[a] = g.o[a] + (double)(idx[a] + ((c >> a) & 1)) * g.h[a];
-      sum = sum + rsp_at(ph, p);
-    }
-    val = sum * (1.0 / (double)nc);
-  }
-  x[j] = (float)val;
-}
-
-void launch_raster(const PhantomDev& ph, float* x, long long nvox, cudaStream_t st) {
-  if (nvox <= 0) return;
-  int threads = 256;
-  long long blocks = (nvox + threads - 1) / threads;
-  k_raster<<<(unsigned)blocks, threads, 0, st>>>(ph, x, nvox);
-}
 
 // ---------------------------------------------------------------------------
 // Sinks of merged entries

@@ -60,4 +60,11 @@ void launch_csr_forward(const long long* row_ptr, const int* col, const float* v
 void launch_csr_adjoint(const long long* row_ptr, const int* col, const float* val, long long row0,
                         long long n, const float* r, float* g, cudaStream_t st);
 
+// string-averaging projections (pct_sap.cu): workspace = M doubles of
+// weights (256-byte aligned) then M x n_cols floats of string iterates
+size_t sap_workspace_bytes(long long n_cols, int M);
+void launch_sap(const long long* row_ptr, const int* col, const float* val, const float* b, long long n_rows,
+                long long n_cols, int M, const double* w_dev, float lambda, int iterations, float* x, void* ws,
+                cudaStream_t st);
+
 }  // namespace pct

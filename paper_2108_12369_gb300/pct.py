@@ -69,7 +69,7 @@ EXPORTS = ["pct_phantom_create", "pct_phantom_destroy", "pct_phantom_nvox", "pct
            "pct_simulate",
            "pct_projector_workspace_size", "pct_forward", "pct_adjoint", "pct_batch_workspace_size", "pct_batch_create",
            "pct_batch_count", "pct_batch_nnz", "pct_batch_fill", "pct_batch_params", "pct_batch_destroy",
-           "pct_scan_counts_static", "pct_last_error", "pct_version"]
+           "pct_scan_counts_static", "pct_sap_workspace_size", "pct_sap", "pct_last_error", "pct_version"]
 BATCH_AUTOTUNE = 1
 STATIC_SCAN_MAX_ROWS = 1 << 28
 
@@ -110,6 +110,9 @@ def lib():
             "pct_batch_fill": ([vp, P(vp), P(vp), P(vp), vp], C.c_int),
             "pct_batch_params": ([vp, P(C.c_int32), P(C.c_int32)], C.c_int),
             "pct_batch_destroy": ([vp], C.c_int),
+            "pct_sap_workspace_size": ([C.c_int64, C.c_int32, P(C.c_size_t)], C.c_int),
+            "pct_sap": ([P(Csr), vp, C.c_int32, P(C.c_double), C.c_double, C.c_int32, vp, vp, C.c_size_t, vp],
+                        C.c_int),
             "pct_last_error": ([], C.c_char_p),
             "pct_version": ([], C.c_char_p),
         }
@@ -372,3 +375,28 @@ def batch_workspace_size(workloads) -> int:
     n = C.c_size_t()
     _check(lib().pct_batch_workspace_size(items, len(phs), C.byref(n)))
     return n.value
+
+
+def sap_workspace_size(n_cols: int, n_strings: int) -> int:
+    n = C.c_size_t()
+    _check(lib().pct_sap_workspace_size(int(n_cols), int(n_strings), C.byref(n)))
+    return n.value
+
+
+def sap(A, b, n_cols: int, n_strings: int, lam: float, iterations: int, x, weights=None, workspace=None,
+        stream=None):
+    """String-averaging projections (Sec. II-D) on the CSR dict A (row_ptr,
+    col, val) and b, in place on the float32 device tensor x."""
+    import torch
+    ws = workspace
+    if ws is None:
+        ws = torch.empty(sap_workspace_size(n_cols, n_strings), dtype=torch.uint8, device=x.device)
+    csr = Csr(A["row_ptr"].numel() - 1, int(n_cols), A["col"].numel(), A["row_ptr"].data_ptr(),
+              A["col"].data_ptr(), A["val"].data_ptr(), 0, 0)
+    wts = None
+    if weights is not None:
+        warr = np.ascontiguousarray(weights, dtype=np.float64)
+        wts = warr.ctypes.data_as(C.POINTER(C.c_double))
+    _check(lib().pct_sap(C.byref(csr), _ptr(b), int(n_strings), wts, float(lam), int(iterations), _ptr(x),
+                         _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+    return x
