@@ -819,7 +819,7 @@ __device__ __forceinline__ void fill_axis(SM& sm, int nseg, int lane, const SimD
 // segment records and the row's entry count.
 // ---------------------------------------------------------------------------
 template <int DIM, class SM>
-__device__ __forceinline__ void coop_count_row(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
+__device__ __forceinline__ bool coop_count_row(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
                                                long long row, SM& sm, long long* __restrict__ counts) {
   using W = SegW<DIM>;
   const int lane = threadIdx.x & 31;
@@ -930,9 +930,18 @@ __device__ __forceinline__ void coop_count_row(const SimDev& S, const MixArgs& M
       for (int q = lane; q < nseg * W::NV; q += 32) d4[q] = src[q];
       if (lane == 0) counts[row] = totE;
       __syncwarp();
-      return;
+      return true;
     }
   }
+  __syncwarp();
+  return false;  // the caller walks it (count_row_walk)
+}
+
+// a row the cooperative count declined: the per-lane walker counts it and
+// marks it for the fill
+template <int DIM>
+__device__ __forceinline__ void count_row_walk(const SimDev* Sg, const MixArgs& M, long long row,
+                                               long long* __restrict__ counts) {
   walk_row_lane0<DIM, false>(Sg, M, row, counts, 0, 0, nullptr, nullptr, nullptr, nullptr);
 }
 
@@ -944,7 +953,7 @@ __device__ __forceinline__ void coop_count_row(const SimDev& S, const MixArgs& M
 // its CSR position; entry 0 of every segment comes from the segment's lane.
 // ---------------------------------------------------------------------------
 template <int DIM, class SM>
-__device__ __forceinline__ void coop_fill_row(const SimDev& S, const MixArgs& M, const SimDev* Sg, long long row,
+__device__ __forceinline__ bool coop_fill_row(const SimDev& S, const MixArgs& M, const SimDev* Sg, long long row,
                                               SM& sm, const long long* __restrict__ row_ptr,
                                               const float* __restrict__ x, int* __restrict__ col,
                                               float* __restrict__ val, float* __restrict__ b) {
@@ -1023,11 +1032,22 @@ __device__ __forceinline__ void coop_fill_row(const SimDev& S, const MixArgs& M,
         }
         if (lane == 0) b[row] = (sum.hi + sum.lo) * r.fac;
         __syncwarp();
-        return;
+        return true;
       }
     }
   }
-  walk_row_lane0<DIM, true>(Sg, M, row, nullptr, rowstart, rowend, x, col, val, b);
+  __syncwarp();
+  return false;  // the caller walks it (fill_row_walk)
+}
+
+// a row the cooperative fill declined (marked by the count, beyond the
+// layout, or a queue overflow): the per-lane walker writes all of it again
+template <int DIM>
+__device__ __forceinline__ void fill_row_walk(const SimDev* Sg, const MixArgs& M, long long row,
+                                              const long long* __restrict__ row_ptr, const float* __restrict__ x,
+                                              int* __restrict__ col, float* __restrict__ val,
+                                              float* __restrict__ b) {
+  walk_row_lane0<DIM, true>(Sg, M, row, nullptr, row_ptr[row], row_ptr[row + 1], x, col, val, b);
 }
 
 }  // namespace pct

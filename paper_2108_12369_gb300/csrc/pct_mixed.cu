@@ -82,11 +82,21 @@ template <int DIM, int CAP>
 __device__ __forceinline__ void rows_block(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
                                            long long n, long long row0, long long* __restrict__ counts) {
   CoopSmem<DIM, CAP>& sm = warp_smem<CoopSmem<DIM, CAP>>();
-  __shared__ int take;
-  if (threadIdx.x == 0) take = 4;
+  __shared__ int take, n_walk;
+  __shared__ unsigned char walk[128];  // rows the cooperative count declined
+  if (threadIdx.x == 0) {
+    take = 4;
+    n_walk = 0;
+  }
   __syncthreads();
   for (int k = threadIdx.x >> 5; k < 128 && row0 + k < n; k = next_row_of_block(&take))
-    coop_count_row<DIM>(S, M, Sg, gdg, row0 + k, sm, counts);
+    if (!coop_count_row<DIM>(S, M, Sg, gdg, row0 + k, sm, counts) && (threadIdx.x & 31) == 0)
+      walk[atomicAdd(&n_walk, 1)] = (unsigned char)k;
+  // the declined rows after all others: the walker's out-of-line call stays
+  // out of the cooperative loop (a call there makes the register allocator
+  // keep the loop's state in local memory)
+  __syncthreads();
+  for (int q = threadIdx.x >> 5; q < n_walk; q += 4) count_row_walk<DIM>(Sg, M, row0 + walk[q], counts);
 }
 
 // The count of one simulation runs as two kernels: the FP64 path set-up
@@ -114,8 +124,12 @@ __device__ __forceinline__ void fill_block(const SimDev& S, const MixArgs& M, co
   FillSmem<DIM, CAP>& sm = warp_smem<FillSmem<DIM, CAP>>();
   const int lane = threadIdx.x & 31;
   const int lines = (M.seg_stride * (int)sizeof(SegG<DIM>) + 127) / 128;
-  __shared__ int take;
-  if (threadIdx.x == 0) take = 4;
+  __shared__ int take, n_walk;
+  __shared__ unsigned char walk[128];  // rows the cooperative fill declined
+  if (threadIdx.x == 0) {
+    take = 4;
+    n_walk = 0;
+  }
   __syncthreads();
   int k = threadIdx.x >> 5;
   while (k < 128 && row0 + k < n) {
@@ -128,9 +142,14 @@ __device__ __forceinline__ void fill_block(const SimDev& S, const MixArgs& M, co
       if (lane < lines) asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + 128 * lane));
       if (lane == 31) asm volatile("prefetch.global.L2 [%0];" ::"l"(M.rdf + rn));
     }
-    coop_fill_row<DIM>(S, M, Sg, row, sm, row_ptr, x, col, val, b);
+    if (!coop_fill_row<DIM>(S, M, Sg, row, sm, row_ptr, x, col, val, b) && lane == 0)
+      walk[atomicAdd(&n_walk, 1)] = (unsigned char)k;
     k = kn;
   }
+  // the declined rows after all others (their out-of-line walker call stays
+  // out of the cooperative loop)
+  __syncthreads();
+  for (int q = threadIdx.x >> 5; q < n_walk; q += 4) fill_row_walk<DIM>(Sg, M, row0 + walk[q], row_ptr, x, col, val, b);
 }
 
 template <int DIM, int CAP>
