@@ -50,10 +50,11 @@ typedef enum {
 } pct_status;
 
 enum { PCT_ELLIPSOID = 0, PCT_EXTRUDED = 1 };                /* phantom kind (3D) */
-enum { PCT_RASTER_CENTER = 0, PCT_RASTER_CORNER = 1 };       /* Sec. II-A options */
+enum { PCT_RASTER_CENTER = 0, PCT_RASTER_CORNER = 1, PCT_RASTER_AREA = 2 }; /* Sec. II-A options */
 enum { PCT_PATH_STRAIGHT = 0, PCT_PATH_STRAIGHT_MCS = 1, PCT_PATH_SPLINE = 2 };
 enum { PCT_CHORD_EXACT = 0, PCT_CHORD_CONSTANT = 1 };        /* Sec. II-C */
 enum { PCT_NOISE_NONE = 0, PCT_NOISE_GAUSS_REL = 1 };
+enum { PCT_MCS_FIXED = 0, PCT_MCS_HIGHLAND = 1 };            /* Sec. II-B exit widths */
 /* Arithmetic form of the path and traversal kernels.  Both give identical
  * voxel indices and row pointers (every crossing decision equals the FP64
  * definition's); values and b agree within 1e-6 relative per row.
@@ -82,17 +83,25 @@ typedef struct {
 typedef struct {
   int32_t dim;    /* 2 or 3 */
   int32_t kind;   /* PCT_ELLIPSOID / PCT_EXTRUDED */
-  int32_t raster; /* PCT_RASTER_CENTER / PCT_RASTER_CORNER */
+  int32_t raster; /* PCT_RASTER_CENTER / PCT_RASTER_CORNER / PCT_RASTER_AREA */
   int32_t n[3];   /* voxels per axis, >= 1, product < 2^31 */
   double h[3];    /* voxel size, mm, > 0 */
   int32_t n_regions;          /* 1..PCT_MAX_REGIONS */
   const pct_region* regions;  /* host array, copied by pct_phantom_create */
+  int32_t area_samples;       /* PCT_RASTER_AREA: sub-samples per axis S, 1..64 */
 } pct_phantom_desc;
 
 /* Sec. II-B.  Lateral entry offsets are uniform on t_range (and v_range in
  * 3D).  MCS models draw, per proton, an entry slope ~ N(0, sigma_in) per
  * plane and a bivariate normal exit pair (displacement ~ N(0, sigma_lat) mm,
- * slope ~ N(0, sigma_out)) with correlation rho per plane.  SPLINE paths are
+ * slope ~ N(0, sigma_out)) with correlation rho per plane.  With mcs =
+ * PCT_MCS_HIGHLAND the exit widths follow the Highland formula with the PDG
+ * constants instead, per proton, from its chord x through the hull (region
+ * 0): theta0 = 13.6 MeV / (beta c p) sqrt(x / X0) (1 + 0.038 ln(x / (X0
+ * beta^2))) for a proton of kinetic energy beam_mev in a medium of radiation
+ * length x0_mm; sigma_out = theta0, sigma_lat = x theta0 / sqrt(3), rho =
+ * sqrt(3) / 2 (a thin slab's displacement-angle covariance); sigma_lat,
+ * sigma_out and rho are then ignored.  SPLINE paths are
  * cubic Hermite curves sampled at spline_segments pieces.  With
  * PCT_NOISE_GAUSS_REL, b_i is multiplied by (1 + noise_rel z_i), z_i ~ N(0,1)
  * (our stand-in for the PSTAR / Tschalar energy-straggling noise of
@@ -106,6 +115,9 @@ typedef struct {
   double v_range[2];
   double sigma_lat, sigma_in, sigma_out, rho; /* |rho| <= 1 */
   double noise_rel;
+  int32_t mcs;       /* PCT_MCS_FIXED (the widths above) or PCT_MCS_HIGHLAND */
+  double beam_mev;   /* PCT_MCS_HIGHLAND: proton kinetic energy, MeV, > 0 */
+  double x0_mm;      /* PCT_MCS_HIGHLAND: radiation length, mm, > 0 (water: 360.8) */
 } pct_path_model;
 
 /* One simulated acquisition, or a contiguous block of one: angles (host,
@@ -156,9 +168,11 @@ pct_status pct_phantom_destroy(pct_phantom* ph);
 /* number of voxels (columns of A), or -1 for NULL */
 int64_t pct_phantom_nvox(const pct_phantom* ph);
 
-/* Sec. II-A: x_true_dev[j] = RSP of voxel j by the phantom's raster option
- * (centre point, or the mean over the 4 / 8 corners), in FP32.  The stored
- * solution vector of the simulator. */
+/* Sec. II-A: x_true_dev[j] = RSP of voxel j by the phantom's raster option,
+ * in FP32: the centre point; the mean over the 4 / 8 corners; or the
+ * weighted-area average sum_r RSP_r f_r, with f_r the fraction of the voxel's
+ * S^dim sub-sample midpoints (o + (i + (k + 1/2) / S) h per axis) whose last
+ * containing region is r.  The stored solution vector of the simulator. */
 pct_status pct_phantom_rasterize(const pct_phantom* ph, float* x_true_dev, void* stream);
 
 /* ---- simulation: A, b (Sec. II-B, II-C) -------------------------------- */
@@ -328,6 +342,22 @@ pct_status pct_scan_counts_static(int64_t* row_ptr_dev, int64_t n_rows, void* st
 pct_status pct_sap_workspace_size(int64_t n_cols, int32_t n_strings, size_t* bytes);
 pct_status pct_sap(const pct_csr* A, const float* b_dev, int32_t n_strings, const double* weights, double lambda,
                    int32_t iterations, float* x_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* ---- the system on disk (Sec. II-C: A written to a file read back as CSR) -
+ * Host memory and host I/O only (no device work).  Layout: a 128-byte header
+ * ("PCTCSR1\0", int64 n_rows, n_cols, nnz, then the byte offsets of the five
+ * sections), then int64 row_ptr [n_rows + 1], int32 col [nnz], float val
+ * [nnz], float b [n_rows], float x_true [n_cols], each section on a 4096-byte
+ * boundary.  pct_csr_file_create makes the file for the whole system and
+ * writes x_true; pct_csr_file_write_rows writes a block of rows (local
+ * row_ptr[0..n_rows], any base, with its col / val / b) at global row row0
+ * and global nonzero offset nz0 -- several writers (the angle blocks of an
+ * acquisition split over GPUs, nz0 from the all-gathered block sizes) fill
+ * one file that equals a single writer's.  EINVAL with the system's message
+ * on I/O errors or a block beyond the file's sizes. */
+pct_status pct_csr_file_create(const char* path, int64_t n_rows, int64_t n_cols, int64_t nnz, const float* x_true);
+pct_status pct_csr_file_write_rows(const char* path, int64_t row0, int64_t n_rows, int64_t nz0,
+                                   const int64_t* row_ptr, const int32_t* col, const float* val, const float* b);
 
 /* message of the calling thread's last failure ("" if none) */
 const char* pct_last_error(void);

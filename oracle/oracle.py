@@ -20,10 +20,11 @@ SRC = HERE / "pct_oracle.c"
 LIB = HERE / "_build" / "liboracle.so"
 
 ELLIPSOID, EXTRUDED = 0, 1
-CENTER, CORNER = 0, 1
+CENTER, CORNER, AREA = 0, 1, 2
 STRAIGHT, STRAIGHT_MCS, SPLINE = 0, 1, 2
 CHORD_EXACT, CHORD_CONSTANT = 0, 1
 NOISE_NONE, NOISE_GAUSS_REL = 0, 1
+MCS_FIXED, MCS_HIGHLAND = 0, 1
 
 
 def build(force: bool = False) -> Path:
@@ -44,7 +45,7 @@ def build(force: bool = False) -> Path:
 class _Phantom(C.Structure):
     _fields_ = [("dim", C.c_int32), ("kind", C.c_int32), ("raster", C.c_int32),
                 ("n", C.c_int32 * 3), ("h", C.c_double * 3), ("n_regions", C.c_int32),
-                ("regions", C.POINTER(C.c_double))]
+                ("regions", C.POINTER(C.c_double)), ("area_samples", C.c_int32)]
 
 
 class _Model(C.Structure):
@@ -52,7 +53,8 @@ class _Model(C.Structure):
                 ("noise", C.c_int32), ("t_lo", C.c_double), ("t_hi", C.c_double),
                 ("v_lo", C.c_double), ("v_hi", C.c_double), ("sigma_lat", C.c_double),
                 ("sigma_in", C.c_double), ("sigma_out", C.c_double), ("rho", C.c_double),
-                ("noise_rel", C.c_double)]
+                ("noise_rel", C.c_double), ("mcs", C.c_int32), ("beam_mev", C.c_double),
+                ("x0_mm", C.c_double)]
 
 
 class _Sim(C.Structure):
@@ -94,6 +96,8 @@ def lib():
         _lib.orc_fill_rows.argtypes = [P(_Sim), P(C.c_int64), C.c_int64, P(C.c_int64),
                                        P(C.c_int32), P(C.c_double), P(C.c_double), P(C.c_double),
                                        C.c_int32]
+        _lib.orc_highland.argtypes = [C.c_double, C.c_double, C.c_double, P(C.c_double)]
+        _lib.orc_highland.restype = C.c_double
         _lib.orc_sap.argtypes = [C.c_int64, C.c_int64, P(C.c_int64), P(C.c_int32), P(C.c_double),
                                  P(C.c_double), C.c_int32, P(C.c_double), C.c_double, C.c_int32,
                                  P(C.c_double)]
@@ -117,7 +121,7 @@ class Phantom:
         self.c = _Phantom(int(desc["dim"]), int(desc.get("kind", ELLIPSOID)),
                           int(desc.get("raster", CORNER)), (C.c_int32 * 3)(*n),
                           (C.c_double * 3)(*h), len(self.regions),
-                          _ptr(self.regions, C.c_double))
+                          _ptr(self.regions, C.c_double), int(desc.get("area_samples", 4)))
         self.nvox = int(np.prod(n[: desc["dim"]]))
 
     def raster(self) -> np.ndarray:
@@ -151,7 +155,8 @@ def _model_struct(m: dict) -> _Model:
                   float(m.get("v_range", (0.0, 0.0))[0]), float(m.get("v_range", (0.0, 0.0))[1]),
                   float(m.get("sigma_lat", 0.0)), float(m.get("sigma_in", 0.0)),
                   float(m.get("sigma_out", 0.0)), float(m.get("rho", 0.0)),
-                  float(m.get("noise_rel", 0.0)))
+                  float(m.get("noise_rel", 0.0)), int(m.get("mcs", MCS_FIXED)),
+                  float(m.get("beam_mev", 200.0)), float(m.get("x0_mm", 360.8)))
 
 
 class Simulation:
@@ -259,3 +264,10 @@ def sap(row_ptr, col, val, b, n_cols: int, n_strings: int, lam: float, iteration
                   _ptr(bb, C.c_double), int(n_strings), None if w is None else _ptr(w, C.c_double),
                   float(lam), int(iterations), _ptr(x, C.c_double))
     return x
+
+
+def highland(beam_mev: float, x0_mm: float, x_mm: float):
+    """(theta0 in rad, beta c p in MeV) of the Highland / PDG formula."""
+    bcp = C.c_double()
+    th = lib().orc_highland(float(beam_mev), float(x0_mm), float(x_mm), C.byref(bcp))
+    return th, bcp.value

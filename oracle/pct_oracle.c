@@ -173,7 +173,15 @@ static double rsp_at(const orc_phantom* ph, const double p[3]) {
   return v;
 }
 
-/* Sec. II-A: centre-point or corner-point-average RSP of every voxel */
+/* the last region containing a point (painter's order), else -1 */
+static int32_t region_at(const orc_phantom* ph, const double p[3]) {
+  int32_t v = -1;
+  for (int32_t r = 0; r < ph->n_regions; ++r)
+    if (inside(ph, r, p)) v = r;
+  return v;
+}
+
+/* Sec. II-A: centre-point, corner-point-average or weighted-area RSP of every voxel */
 void orc_raster(const orc_phantom* ph, double* x) {
   grid_t g = grid_of(ph);
   int nz = (g.dim == 3) ? g.n[2] : 1;
@@ -187,6 +195,26 @@ void orc_raster(const orc_phantom* ph, double* x) {
         if (ph->raster == ORC_CENTER) {
           for (int a = 0; a < g.dim; ++a) p[a] = g.o[a] + ((double)idx[a] + 0.5) * g.h[a];
           x[j] = rsp_at(ph, p);
+        } else if (ph->raster == ORC_AREA) {
+          /* area fractions from the sub-sample midpoints
+             p_a = o_a + (i_a + (k_a + 1/2) / S) h_a, k_a = 0 .. S - 1 */
+          int S = ph->area_samples;
+          int64_t cnt[64];
+          for (int r = 0; r < ph->n_regions; ++r) cnt[r] = 0;
+          int kzn = (g.dim == 3) ? S : 1;
+          for (int kz = 0; kz < kzn; ++kz)
+            for (int ky = 0; ky < S; ++ky)
+              for (int kx = 0; kx < S; ++kx) {
+                int k[3] = {kx, ky, kz};
+                for (int a = 0; a < g.dim; ++a)
+                  p[a] = g.o[a] + ((double)idx[a] + ((double)k[a] + 0.5) / (double)S) * g.h[a];
+                int32_t r = region_at(ph, p);
+                if (r >= 0) cnt[r]++;
+              }
+          double nsub = (double)S * (double)S * (g.dim == 3 ? (double)S : 1.0);
+          double sum = 0.0;
+          for (int r = 0; r < ph->n_regions; ++r) sum = sum + ph->regions[7 * r + 6] * (double)cnt[r];
+          x[j] = sum / nsub;
         } else {
           double sum = 0.0;
           for (int c = 0; c < ncorner; ++c) {
@@ -356,9 +384,25 @@ int64_t orc_segment(const orc_phantom* ph, const double P[3], const double Q[3],
 /* ------------------------------------------------------------------------- */
 typedef struct {
   double t, v;
-  double lat_t, ang_t, lat_v, ang_v, in_t, in_v;
+  double zt1, zt2, zv1, zv2;  /* exit pairs (ut-plane, uv-plane), standard normals */
+  double in_t, in_v;
   double z_noise;
 } draws_t;
+
+/* Highland's formula with the PDG constants (Sec. II-B): theta0 =
+   13.6 MeV / (beta c p) sqrt(x / X0) (1 + 0.038 ln(x / (X0 beta^2))) for a
+   singly charged particle; beta c p = (pc)^2 / E with (pc)^2 = T (T + 2 m),
+   E = T + m, m = 938.272088 MeV (proton). */
+static const double ORC_MP_MEV = 938.272088;
+double orc_highland(double beam_mev, double x0_mm, double x_mm, double* beta_cp) {
+  double E = beam_mev + ORC_MP_MEV;
+  double pc2 = beam_mev * (beam_mev + 2.0 * ORC_MP_MEV);
+  double bcp = pc2 / E;
+  double beta2 = pc2 / (E * E);
+  if (beta_cp) *beta_cp = bcp;
+  double t = x_mm / x0_mm;
+  return (13.6 / bcp) * sqrt(t) * (1.0 + 0.038 * orc_log(t / beta2));
+}
 
 static draws_t draw_row(const orc_sim* sim, int64_t row) {
   const orc_model* md = sim->model;
@@ -373,15 +417,14 @@ static draws_t draw_row(const orc_sim* sim, int64_t row) {
   }
   uint64_t j = 4;
   double z[2];
-  double r = sqrt(1.0 - md->rho * md->rho);
   if (md->model != ORC_STRAIGHT) {
     j = orc_normal_pairs(sim->seed, sim->stream, (uint64_t)row, j, 1, z);
-    d.lat_t = md->sigma_lat * z[0];
-    d.ang_t = md->sigma_out * (md->rho * z[0] + r * z[1]);
+    d.zt1 = z[0];
+    d.zt2 = z[1];
     if (dim == 3) {
       j = orc_normal_pairs(sim->seed, sim->stream, (uint64_t)row, j, 1, z);
-      d.lat_v = md->sigma_lat * z[0];
-      d.ang_v = md->sigma_out * (md->rho * z[0] + r * z[1]);
+      d.zv1 = z[0];
+      d.zv2 = z[1];
     }
     j = orc_normal_pairs(sim->seed, sim->stream, (uint64_t)row, j, 1, z);
     d.in_t = md->sigma_in * z[0];
@@ -443,6 +486,23 @@ int32_t orc_path(const orc_sim* sim, int64_t row, double* verts, int32_t cap) {
       P0[a] = A[a] + lam_in * g0[a];
       Q1[a] = A[a] + lam_out * g0[a];
     }
+    /* exit pair widths and correlation: fixed by the model, or (Highland)
+       from the chord x through the hull: sigma_angle = theta0(x), sigma_lat
+       = x theta0 / sqrt(3), correlation sqrt(3) / 2 (thin-slab MCS) */
+    double s_lat = md->sigma_lat, s_ang = md->sigma_out, rho = md->rho;
+    if (md->mcs == ORC_MCS_HIGHLAND) {
+      double gl2 = 0.0;
+      for (int a = 0; a < dim; ++a) gl2 = gl2 + g0[a] * g0[a];
+      double x = (lam_out - lam_in) * sqrt(gl2);
+      s_ang = orc_highland(md->beam_mev, md->x0_mm, x, NULL);
+      s_lat = x * s_ang * (1.0 / sqrt(3.0));
+      rho = 0.5 * sqrt(3.0);
+    }
+    double rc = sqrt(1.0 - rho * rho);
+    double lat_t = s_lat * d.zt1;
+    double ang_t = s_ang * (rho * d.zt1 + rc * d.zt2);
+    double lat_v = s_lat * d.zv1;
+    double ang_v = s_ang * (rho * d.zv1 + rc * d.zv2);
     nt[0] = -g0[1];
     nt[1] = g0[0];
     nt[2] = 0.0;
@@ -451,13 +511,13 @@ int32_t orc_path(const orc_sim* sim, int64_t row, double* verts, int32_t cap) {
       nvv[1] = -(g0[2] * g0[1]);
       nvv[2] = g0[0] * g0[0] + g0[1] * g0[1];
       for (int a = 0; a < 3; ++a) {
-        P1[a] = (Q1[a] + d.lat_t * nt[a]) + d.lat_v * nvv[a];
-        g1[a] = (g0[a] + d.ang_t * nt[a]) + d.ang_v * nvv[a];
+        P1[a] = (Q1[a] + lat_t * nt[a]) + lat_v * nvv[a];
+        g1[a] = (g0[a] + ang_t * nt[a]) + ang_v * nvv[a];
       }
     } else {
       for (int a = 0; a < 2; ++a) {
-        P1[a] = Q1[a] + d.lat_t * nt[a];
-        g1[a] = g0[a] + d.ang_t * nt[a];
+        P1[a] = Q1[a] + lat_t * nt[a];
+        g1[a] = g0[a] + ang_t * nt[a];
       }
       P1[2] = 0.0;
       g1[2] = 0.0;

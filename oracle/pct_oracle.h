@@ -30,19 +30,21 @@ extern "C" {
 #endif
 
 enum { ORC_ELLIPSOID = 0, ORC_EXTRUDED = 1 };
-enum { ORC_CENTER = 0, ORC_CORNER = 1 };
+enum { ORC_CENTER = 0, ORC_CORNER = 1, ORC_AREA = 2 };
 enum { ORC_STRAIGHT = 0, ORC_STRAIGHT_MCS = 1, ORC_SPLINE = 2 };
 enum { ORC_CHORD_EXACT = 0, ORC_CHORD_CONSTANT = 1 };
 enum { ORC_NOISE_NONE = 0, ORC_NOISE_GAUSS_REL = 1 };
+enum { ORC_MCS_FIXED = 0, ORC_MCS_HIGHLAND = 1 };
 
 typedef struct {
   int32_t dim;        /* 2 or 3 */
   int32_t kind;       /* ORC_ELLIPSOID or ORC_EXTRUDED (3D: z ignored) */
-  int32_t raster;     /* ORC_CENTER or ORC_CORNER */
+  int32_t raster;     /* ORC_CENTER, ORC_CORNER or ORC_AREA */
   int32_t n[3];       /* voxels per axis (n[2] = 1 in 2D) */
   double h[3];        /* voxel size per axis, mm */
   int32_t n_regions;  /* regions in painter's order; region 0 is the hull */
   const double* regions; /* n_regions x 7: cx cy cz ax ay az rsp */
+  int32_t area_samples;  /* ORC_AREA: sub-samples per axis, S */
 } orc_phantom;
 
 typedef struct {
@@ -57,6 +59,10 @@ typedef struct {
   double sigma_out;        /* exit slope sigma (rad) */
   double rho;              /* correlation of exit (displacement, slope) */
   double noise_rel;        /* relative WEPL noise sigma */
+  int32_t mcs;             /* ORC_MCS_FIXED: the sigmas and rho above; ORC_MCS_HIGHLAND:
+                              per proton from its chord through the hull (Highland / PDG) */
+  double beam_mev;         /* proton kinetic energy, MeV (HIGHLAND) */
+  double x0_mm;            /* radiation length of the (water-equivalent) medium, mm (HIGHLAND) */
 } orc_model;
 
 typedef struct {
@@ -84,7 +90,17 @@ uint64_t orc_normal_pairs(uint64_t seed, uint64_t stream, uint64_t row, uint64_t
 int orc_hull_hit(const orc_phantom* ph, int32_t r, const double A[3], const double g[3],
                  double* lam_in, double* lam_out);
 
-/* phantom raster: x[j] in FP64 (the stored x_true is its FP32 rounding) */
+/* Highland / PDG multiple-scattering width theta0 (rad) of a proton of kinetic
+   energy beam_mev after x_mm of a medium of radiation length x0_mm (Sec.
+   II-B, MCS); *beta_cp receives beta c p in MeV.  Parity partly pinned: the
+   kinematics by an independent route, the formula by its scaling. */
+double orc_highland(double beam_mev, double x0_mm, double x_mm, double* beta_cp);
+
+/* phantom raster: x[j] in FP64 (the stored x_true is its FP32 rounding).
+   ORC_AREA (weighted-area average, Sec. II-A): x = sum_r rsp_r f_r over the
+   regions in order, f_r the fraction of the voxel's S^dim sub-sample
+   midpoints whose last containing region is r, evaluated as
+   (sum_r rsp_r count_r) / S^dim. */
 void orc_raster(const orc_phantom* ph, double* x);
 
 /* one segment P->Q through the grid: voxel ids and FP64 chord lengths in path

@@ -61,8 +61,10 @@ extern "C" pct_status pct_phantom_create(const pct_phantom_desc* d, pct_phantom*
   *out = nullptr;
   if (d->dim != 2 && d->dim != 3) return fail(PCT_EINVAL, "dim must be 2 or 3 (got %d)", d->dim);
   if (d->kind != PCT_ELLIPSOID && d->kind != PCT_EXTRUDED) return fail(PCT_EINVAL, "bad phantom kind %d", d->kind);
-  if (d->raster != PCT_RASTER_CENTER && d->raster != PCT_RASTER_CORNER)
+  if (d->raster != PCT_RASTER_CENTER && d->raster != PCT_RASTER_CORNER && d->raster != PCT_RASTER_AREA)
     return fail(PCT_EINVAL, "bad raster option %d", d->raster);
+  if (d->raster == PCT_RASTER_AREA && (d->area_samples < 1 || d->area_samples > 64))
+    return fail(PCT_EINVAL, "area_samples = %d outside 1..64", d->area_samples);
   long long nvox = 1;
   for (int a = 0; a < d->dim; ++a) {
     if (d->n[a] < 1) return fail(PCT_EINVAL, "n[%d] = %d must be >= 1", a, d->n[a]);
@@ -102,6 +104,7 @@ extern "C" pct_status pct_phantom_create(const pct_phantom_desc* d, pct_phantom*
   }
   pd.kind = d->kind;
   pd.raster = d->raster;
+  pd.area_s = d->raster == PCT_RASTER_AREA ? d->area_samples : 1;
   pd.n_regions = d->n_regions;
   for (int r = 0; r < d->n_regions; ++r) {
     for (int a = 0; a < 3; ++a) {
@@ -167,6 +170,9 @@ pct_status check_geometry(const pct_phantom* ph, const pct_geometry* g, int prec
   for (double s : sig)
     if (!std::isfinite(s) || s < 0.0) return fail(PCT_EINVAL, "sigmas must be finite and >= 0");
   if (!std::isfinite(m.rho) || m.rho < -1.0 || m.rho > 1.0) return fail(PCT_EINVAL, "rho must lie in [-1, 1]");
+  if (m.mcs != PCT_MCS_FIXED && m.mcs != PCT_MCS_HIGHLAND) return fail(PCT_EINVAL, "bad mcs option %d", m.mcs);
+  if (m.mcs == PCT_MCS_HIGHLAND && !(finite_pos(m.beam_mev) && finite_pos(m.x0_mm)))
+    return fail(PCT_EINVAL, "Highland widths need beam_mev > 0 and x0_mm > 0");
   return PCT_OK;
 }
 
@@ -221,6 +227,20 @@ pct_status make_sim(const pct_phantom* ph, const pct_geometry* g, int precision,
   S.md.rho = m.rho;
   S.md.rho_c = std::sqrt(1.0 - m.rho * m.rho);
   S.md.noise_rel = m.noise_rel;
+  // Highland / PDG constants (host FP64, the expressions of the definition):
+  // E = T + m_p, (pc)^2 = T (T + 2 m_p), beta c p = (pc)^2 / E, beta^2 = (pc)^2 / E^2
+  S.md.mcs = m.mcs;
+  if (m.mcs == PCT_MCS_HIGHLAND) {
+    const double mp = 938.272088;  // proton mass, MeV (PDG)
+    const double E = m.beam_mev + mp;
+    const double pc2 = m.beam_mev * (m.beam_mev + 2.0 * mp);
+    S.md.hl_k = 13.6 / (pc2 / E);
+    S.md.hl_x0 = m.x0_mm;
+    S.md.hl_beta2 = pc2 / (E * E);
+    S.md.hl_s3 = 1.0 / std::sqrt(3.0);
+    S.md.hl_rho = 0.5 * std::sqrt(3.0);
+    S.md.hl_rho_c = std::sqrt(1.0 - S.md.hl_rho * S.md.hl_rho);
+  }
   S.n_angles = g->n_angles;
   S.P = g->paths_per_angle;
   S.seed = g->seed;

@@ -31,6 +31,7 @@ struct GridDev {
 struct PhantomDev {
   GridDev g;
   int kind, raster, n_regions;
+  int area_s;  // weighted-area raster: sub-samples per axis
   double c[kMaxRegions][3];
   double a[kMaxRegions][3];
   double ra[kMaxRegions][3];  // 1 / a, formed on the host (IEEE division)
@@ -43,6 +44,11 @@ struct ModelDev {
   double t_span, v_span;  // t_hi - t_lo, v_hi - v_lo (formed on the host, the same FP64 values)
   double sigma_lat, sigma_in, sigma_out, rho, rho_c;  // rho_c = sqrt(1 - rho^2)
   double noise_rel;
+  // PCT_MCS_HIGHLAND: widths from the chord x through the hull, with host
+  // constants hl_k = 13.6 / (beta c p), hl_x0, hl_beta2, hl_s3 = 1 / sqrt(3),
+  // hl_rho = sqrt(3) / 2, hl_rho_c = sqrt(1 - hl_rho^2)
+  int mcs;
+  double hl_k, hl_x0, hl_beta2, hl_s3, hl_rho, hl_rho_c;
 };
 
 // cubic Hermite basis at one sample s = j / K
@@ -268,17 +274,11 @@ __device__ __forceinline__ PathF64 path_setup(const SimDev& S, long long row) {
   double v = 0.0;
   if (dim == 3) v = md.v_lo + md.v_span * us.get(1);
   long long j = 4;
-  double lat_t = 0.0, ang_t = 0.0, lat_v = 0.0, ang_v = 0.0, in_t = 0.0, in_v = 0.0;
+  double zt1 = 0.0, zt2 = 0.0, zv1 = 0.0, zv2 = 0.0, in_t = 0.0, in_v = 0.0;
   double z1, z2;
   if (md.model != PCT_PATH_STRAIGHT) {
-    normal_pair(us, j, z1, z2);
-    lat_t = md.sigma_lat * z1;
-    ang_t = md.sigma_out * (md.rho * z1 + md.rho_c * z2);
-    if (dim == 3) {
-      normal_pair(us, j, z1, z2);
-      lat_v = md.sigma_lat * z1;
-      ang_v = md.sigma_out * (md.rho * z1 + md.rho_c * z2);
-    }
+    normal_pair(us, j, zt1, zt2);  // exit pair, ut-plane
+    if (dim == 3) normal_pair(us, j, zv1, zv2);  // exit pair, uv-plane
     normal_pair(us, j, z1, z2);
     in_t = md.sigma_in * z1;
     in_v = md.sigma_in * z2;
@@ -316,6 +316,22 @@ __device__ __forceinline__ PathF64 path_setup(const SimDev& S, long long row) {
     p.P0[a] = a < dim ? p.A[a] + lam_in * p.g0[a] : 0.0;
     Q1[a] = a < dim ? p.A[a] + lam_out * p.g0[a] : 0.0;
   }
+  // exit pair widths: fixed, or (Highland) from the chord x through the hull
+  double s_lat = md.sigma_lat, s_ang = md.sigma_out, rho = md.rho, rho_c = md.rho_c;
+  if (md.mcs == PCT_MCS_HIGHLAND) {
+    double gl2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (a < dim) gl2 = gl2 + p.g0[a] * p.g0[a];
+    const double x = (lam_out - lam_in) * sqrt(gl2);
+    const double t = x / md.hl_x0;
+    s_ang = md.hl_k * sqrt(t) * (1.0 + 0.038 * own_log(t / md.hl_beta2));
+    s_lat = x * s_ang * md.hl_s3;
+    rho = md.hl_rho;
+    rho_c = md.hl_rho_c;
+  }
+  const double lat_t = s_lat * zt1, ang_t = s_ang * (rho * zt1 + rho_c * zt2);
+  const double lat_v = s_lat * zv1, ang_v = s_ang * (rho * zv1 + rho_c * zv2);
   nt[0] = -p.g0[1];
   nt[1] = p.g0[0];
   nt[2] = 0.0;

@@ -1,6 +1,7 @@
 // pct_raster.cu -- the NEO phantom raster x_true (Sec. II-A): RSP of every
-// voxel by its centre point, or the mean of its 2^dim corner points, regions
-// painted in order (the last region containing a point gives its RSP).
+// voxel by its centre point, the mean of its 2^dim corner points, or the
+// weighted-area average over S^dim sub-sample midpoints; regions painted in
+// order (the last region containing a point gives its RSP).
 //
 // Definition (FP64): point p_a = o_a + k_a h_a (k_a = index, or index + 1/2
 // for the centre); p lies in region r when sum_a ((p_a - c_a) / a_a)^2 <= 1,
@@ -129,9 +130,54 @@ __global__ void __launch_bounds__(256) k_raster_tile(PhantomDev ph, float* __res
   }
 }
 
+// Weighted-area raster: thread per voxel, S^dim sub-sample midpoints, each
+// classified by region_of; x = (sum_r rsp_r count_r) / S^dim in FP64, the
+// regions in order (the counts are exact, so the result is the definition's).
+template <int DIM>
+__global__ void __launch_bounds__(256) k_raster_area(PhantomDev ph, float* __restrict__ x, long long nvox) {
+  __shared__ double u[64];                   // (k + 1/2) / S
+  __shared__ int cnt[kMaxRegions][256];      // per thread: sub-samples per region
+  const int S = ph.area_s;
+  for (int k = threadIdx.x; k < S; k += blockDim.x) u[k] = ((double)k + 0.5) / (double)S;
+  for (int r = 0; r < ph.n_regions; ++r) cnt[r][threadIdx.x] = 0;
+  __syncthreads();
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= nvox) return;
+  const GridDev& g = ph.g;
+  const int axes = (DIM == 3 && ph.kind == PCT_ELLIPSOID) ? 3 : 2;
+  const int ix = (int)(j % g.n[0]);
+  const long long q = j / g.n[0];
+  const int iy = (int)(q % g.n[1]);
+  const int iz = DIM == 3 ? (int)(q / g.n[1]) : 0;
+  double p[3] = {0.0, 0.0, 0.0};
+  for (int kz = 0; kz < (DIM == 3 ? S : 1); ++kz) {
+    if (DIM == 3) p[2] = g.o[2] + ((double)iz + u[kz]) * g.h[2];
+    for (int ky = 0; ky < S; ++ky) {
+      p[1] = g.o[1] + ((double)iy + u[ky]) * g.h[1];
+      for (int kx = 0; kx < S; ++kx) {
+        p[0] = g.o[0] + ((double)ix + u[kx]) * g.h[0];
+        const int r = region_of(ph, axes, p);
+        if (r >= 0) ++cnt[r][threadIdx.x];
+      }
+    }
+  }
+  const double nsub = (double)S * (double)S * (DIM == 3 ? (double)S : 1.0);
+  double sum = 0.0;
+  for (int r = 0; r < ph.n_regions; ++r) sum = sum + ph.rsp[r] * (double)cnt[r][threadIdx.x];
+  x[j] = (float)(sum / nsub);
+}
+
 void launch_raster(const PhantomDev& ph, float* x, long long nvox, cudaStream_t st) {
   if (nvox <= 0) return;
   const GridDev& g = ph.g;
+  if (ph.raster == PCT_RASTER_AREA) {
+    const unsigned blocks = (unsigned)((nvox + 255) / 256);
+    if (g.dim == 3)
+      k_raster_area<3><<<blocks, 256, 0, st>>>(ph, x, nvox);
+    else
+      k_raster_area<2><<<blocks, 256, 0, st>>>(ph, x, nvox);
+    return;
+  }
   if (g.dim == 3) {
     using T = Tile<3>;
     const long long tiles = (long long)((g.n[0] + T::TX - 1) / T::TX) * ((g.n[1] + T::TY - 1) / T::TY) *

@@ -33,14 +33,15 @@ class Region(C.Structure):
 class PhantomDesc(C.Structure):
     _fields_ = [("dim", C.c_int32), ("kind", C.c_int32), ("raster", C.c_int32),
                 ("n", C.c_int32 * 3), ("h", C.c_double * 3), ("n_regions", C.c_int32),
-                ("regions", C.POINTER(Region))]
+                ("regions", C.POINTER(Region)), ("area_samples", C.c_int32)]
 
 
 class PathModel(C.Structure):
     _fields_ = [("model", C.c_int32), ("chord", C.c_int32), ("spline_segments", C.c_int32),
                 ("noise", C.c_int32), ("t_range", C.c_double * 2), ("v_range", C.c_double * 2),
                 ("sigma_lat", C.c_double), ("sigma_in", C.c_double), ("sigma_out", C.c_double),
-                ("rho", C.c_double), ("noise_rel", C.c_double)]
+                ("rho", C.c_double), ("noise_rel", C.c_double), ("mcs", C.c_int32), ("beam_mev", C.c_double),
+                ("x0_mm", C.c_double)]
 
 
 class Geometry(C.Structure):
@@ -69,7 +70,8 @@ EXPORTS = ["pct_phantom_create", "pct_phantom_destroy", "pct_phantom_nvox", "pct
            "pct_simulate",
            "pct_projector_workspace_size", "pct_forward", "pct_adjoint", "pct_batch_workspace_size", "pct_batch_create",
            "pct_batch_count", "pct_batch_nnz", "pct_batch_fill", "pct_batch_params", "pct_batch_destroy",
-           "pct_scan_counts_static", "pct_sap_workspace_size", "pct_sap", "pct_last_error", "pct_version"]
+           "pct_scan_counts_static", "pct_sap_workspace_size", "pct_sap", "pct_csr_file_create",
+           "pct_csr_file_write_rows", "pct_last_error", "pct_version"]
 BATCH_AUTOTUNE = 1
 STATIC_SCAN_MAX_ROWS = 1 << 28
 
@@ -113,6 +115,8 @@ def lib():
             "pct_sap_workspace_size": ([C.c_int64, C.c_int32, P(C.c_size_t)], C.c_int),
             "pct_sap": ([P(Csr), vp, C.c_int32, P(C.c_double), C.c_double, C.c_int32, vp, vp, C.c_size_t, vp],
                         C.c_int),
+            "pct_csr_file_create": ([C.c_char_p, C.c_int64, C.c_int64, C.c_int64, vp], C.c_int),
+            "pct_csr_file_write_rows": ([C.c_char_p, C.c_int64, C.c_int64, C.c_int64, vp, vp, vp, vp], C.c_int),
             "pct_last_error": ([], C.c_char_p),
             "pct_version": ([], C.c_char_p),
         }
@@ -163,7 +167,7 @@ class Phantom:
         h = list(desc["h"]) + [1.0] * (3 - len(desc["h"]))
         self._desc = PhantomDesc(desc["dim"], desc.get("kind", W.ELLIPSOID), desc.get("raster", W.CORNER),
                                  (C.c_int32 * 3)(*n), (C.c_double * 3)(*h), len(regs),
-                                 C.cast(self._regs, C.POINTER(Region)))
+                                 C.cast(self._regs, C.POINTER(Region)), int(desc.get("area_samples", 4)))
         self.handle = C.c_void_p()
         _check(lib().pct_phantom_create(C.byref(self._desc), C.byref(self.handle)))
         self.nvox = int(lib().pct_phantom_nvox(self.handle))
@@ -195,7 +199,8 @@ class GeometryArgs:
                        m.get("noise", W.NOISE_NONE), (C.c_double * 2)(*m["t_range"]),
                        (C.c_double * 2)(*m.get("v_range", (0.0, 0.0))), m.get("sigma_lat", 0.0),
                        m.get("sigma_in", 0.0), m.get("sigma_out", 0.0), m.get("rho", 0.0),
-                       m.get("noise_rel", 0.0))
+                       m.get("noise_rel", 0.0), m.get("mcs", W.MCS_FIXED), m.get("beam_mev", 200.0),
+                       m.get("x0_mm", W.X0_WATER_MM))
         self.c = Geometry(self.angles.ctypes.data_as(C.POINTER(C.c_double)), len(self.angles),
                           int(w["paths_per_angle"]), pm, C.c_uint64(int(w["seed"])),
                           C.c_uint64(int(stream_id)), int(w.get("first_row", 0)))
@@ -400,3 +405,45 @@ def sap(A, b, n_cols: int, n_strings: int, lam: float, iterations: int, x, weigh
     _check(lib().pct_sap(C.byref(csr), _ptr(b), int(n_strings), wts, float(lam), int(iterations), _ptr(x),
                          _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
     return x
+
+
+def _host_ptr(a):
+    """data pointer of a host numpy array or CPU tensor (None for None)"""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda:
+            raise ValueError("host arrays expected")
+        return C.c_void_p(a.data_ptr())
+    return C.c_void_p(a.ctypes.data)
+
+
+def csr_file_create(path, n_rows: int, n_cols: int, nnz: int, x_true):
+    """pct_csr_file_create: the file of an n_rows x n_cols system with nnz
+    nonzeros, with x_true (host float32) written."""
+    x = np.ascontiguousarray(x_true, dtype=np.float32) if not hasattr(x_true, "data_ptr") else x_true
+    _check(lib().pct_csr_file_create(str(path).encode(), int(n_rows), int(n_cols), int(nnz), _host_ptr(x)))
+
+
+def csr_file_write_rows(path, row0: int, nz0: int, row_ptr, col, val, b):
+    """pct_csr_file_write_rows: a block of rows (host arrays; row_ptr local,
+    any base) at global row row0 and global nonzero offset nz0."""
+    arrs = [np.ascontiguousarray(a, dtype=t) if not hasattr(a, "data_ptr") else a
+            for a, t in ((row_ptr, np.int64), (col, np.int32), (val, np.float32), (b, np.float32))]
+    n = (arrs[0].numel() if hasattr(arrs[0], "numel") else len(arrs[0])) - 1
+    _check(lib().pct_csr_file_write_rows(str(path).encode(), int(row0), int(n), int(nz0),
+                                         *[_host_ptr(a) for a in arrs]))
+
+
+def csr_file_read(path):
+    """The system in a file made by csr_file_create / _write_rows, as numpy
+    arrays mapped from the file: dict(row_ptr, col, val, b, x_true)."""
+    with open(path, "rb") as f:
+        head = f.read(128)
+    if head[:8] != b"PCTCSR1\0":
+        raise ValueError(f"{path} is not a libpct CSR file")
+    n_rows, n_cols, nnz, o_rp, o_col, o_val, o_b, o_x = np.frombuffer(head[8:72], dtype="<i8")
+    mm = lambda off, dt, n: np.memmap(path, dtype=dt, mode="r", offset=int(off), shape=(int(n),))
+    return {"row_ptr": mm(o_rp, "<i8", n_rows + 1), "col": mm(o_col, "<i4", nnz), "val": mm(o_val, "<f4", nnz),
+            "b": mm(o_b, "<f4", n_rows), "x_true": mm(o_x, "<f4", n_cols),
+            "n_rows": int(n_rows), "n_cols": int(n_cols), "nnz": int(nnz)}

@@ -26,10 +26,12 @@ import math
 import numpy as np
 
 ELLIPSOID, EXTRUDED = 0, 1
-CENTER, CORNER = 0, 1
+CENTER, CORNER, AREA = 0, 1, 2
 STRAIGHT, STRAIGHT_MCS, SPLINE = 0, 1, 2
 CHORD_EXACT, CHORD_CONSTANT = 0, 1
 NOISE_NONE, NOISE_GAUSS_REL = 0, 1
+MCS_FIXED, MCS_HIGHLAND = 0, 1
+X0_WATER_MM = 360.8  # radiation length of water (PDG)
 
 BASE_SEED = 210812369
 
@@ -57,12 +59,13 @@ def neo_regions(skin: bool, scale: float = 1.0):
 
 
 def phantom(dim: int, n, h, skin: bool, kind: int = ELLIPSOID, raster: int = CORNER,
-            scale: float = 1.0):
+            scale: float = 1.0, area_samples: int = 4):
+    """area_samples: sub-samples per axis of the weighted-area raster (AREA)."""
     n = tuple(int(v) for v in n)
     h = tuple(float(v) for v in h)
     return {"dim": int(dim), "kind": int(kind), "raster": int(raster),
             "n": n + (1,) * (3 - len(n)), "h": h + (1.0,) * (3 - len(h)),
-            "regions": neo_regions(skin, scale)}
+            "regions": neo_regions(skin, scale), "area_samples": int(area_samples)}
 
 
 def angles(n_angles: int) -> np.ndarray:
@@ -71,13 +74,18 @@ def angles(n_angles: int) -> np.ndarray:
 
 
 def model(kind: int, t_range, v_range=(0.0, 0.0), sigma_lat=0.0, sigma_in=0.0, sigma_out=0.0,
-          rho=0.0, spline_segments=32, chord=CHORD_EXACT, noise_rel=0.0):
+          rho=0.0, spline_segments=32, chord=CHORD_EXACT, noise_rel=0.0, mcs=MCS_FIXED,
+          beam_mev=200.0, x0_mm=X0_WATER_MM):
+    """Path model.  mcs = MCS_HIGHLAND replaces sigma_lat, sigma_out and rho
+    per proton by the Highland / PDG widths for its chord through the hull
+    (beam kinetic energy beam_mev, radiation length x0_mm)."""
     return {"model": int(kind), "chord": int(chord), "spline_segments": int(spline_segments),
             "noise": NOISE_GAUSS_REL if noise_rel > 0 else NOISE_NONE,
             "t_range": (float(t_range[0]), float(t_range[1])),
             "v_range": (float(v_range[0]), float(v_range[1])),
             "sigma_lat": float(sigma_lat), "sigma_in": float(sigma_in),
-            "sigma_out": float(sigma_out), "rho": float(rho), "noise_rel": float(noise_rel)}
+            "sigma_out": float(sigma_out), "rho": float(rho), "noise_rel": float(noise_rel),
+            "mcs": int(mcs), "beam_mev": float(beam_mev), "x0_mm": float(x0_mm)}
 
 
 def neo1_2d_straight(n_angles: int = 180, paths_per_angle: int = 500):

@@ -45,7 +45,8 @@ def test_phantom_create_validates(pct):
     assert ph.nvox == 40000
     ph3 = pct.Phantom(W.phantom(3, (20, 30, 40), (1.0, 1.0, 1.0), skin=True))
     assert ph3.nvox == 24000
-    for bad in ({"dim": 4}, {"n": (0, 10, 1)}, {"h": (1.0, -1.0, 1.0)}, {"raster": 7}, {"kind": 9}):
+    for bad in ({"dim": 4}, {"n": (0, 10, 1)}, {"h": (1.0, -1.0, 1.0)}, {"raster": 7}, {"kind": 9},
+                {"raster": W.AREA, "area_samples": 0}, {"raster": W.AREA, "area_samples": 65}):
         d = dict(W.phantom(2, (10, 10), (1.0, 1.0), skin=False), **bad)
         with pytest.raises(pct.PctError) as e:
             pct.Phantom(d)
@@ -70,7 +71,9 @@ def test_workspace_size_and_geometry_checks(pct):
         assert n >= 10 * 16 + 33 * 32
     bad_models = [dict(w["model"], model=5), dict(w["model"], spline_segments=0),
                   dict(w["model"], rho=1.5), dict(w["model"], sigma_lat=-1.0),
-                  dict(w["model"], t_range=(5.0, -5.0)), dict(w["model"], chord=3)]
+                  dict(w["model"], t_range=(5.0, -5.0)), dict(w["model"], chord=3),
+                  dict(w["model"], mcs=2), dict(w["model"], mcs=W.MCS_HIGHLAND, beam_mev=0.0),
+                  dict(w["model"], mcs=W.MCS_HIGHLAND, x0_mm=float("nan"))]
     for m in bad_models:
         g = pct.GeometryArgs(dict(w, model=m))
         with pytest.raises(pct.PctError) as e:

@@ -54,6 +54,10 @@ def run_oracle(orc, w, rows=None, threads=8):
     W.phantom(2, (200, 160), (1.0, 1.0), skin=True, raster=W.CENTER),
     W.phantom(3, (60, 60, 48), (3.3, 3.3, 3.4), skin=False),
     W.phantom(3, (40, 40, 32), (5.0, 5.0, 5.0), skin=True, kind=W.EXTRUDED, raster=W.CENTER),
+    W.phantom(2, (200, 160), (1.0, 1.0), skin=True, raster=W.AREA, area_samples=8),
+    W.phantom(2, (96, 96), (2.0, 2.0), skin=False, raster=W.AREA, area_samples=5),
+    W.phantom(3, (50, 50, 40), (4.0, 4.0, 4.0), skin=True, raster=W.AREA, area_samples=3),
+    W.phantom(3, (40, 40, 32), (5.0, 5.0, 5.0), skin=False, kind=W.EXTRUDED, raster=W.AREA, area_samples=4),
 ])
 def test_raster_bit_exact(pct, orc, desc):
     ph = pct.Phantom(desc)
@@ -95,6 +99,34 @@ def test_head_3d_reduced(pct, orc, prec, model):
     ref = run_oracle(orc, w)
     st = compare(g, ref, exact_values=(prec == "f64"))
     print(prec, model, st)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("case", ["neo2_spline", "head_3d_straight_mcs"])
+def test_highland_widths(pct, orc, prec, case):
+    """Exit widths from the Highland / PDG formula per proton (Sec. II-B),
+    200 MeV in water; the FP64 form bit for bit, the mixed form within 1e-6."""
+    if case == "neo2_spline":
+        w = W.neo2_2d_spline(n_angles=24, paths_per_angle=301, n=256, h=0.8)
+        w["model"] = dict(w["model"], mcs=W.MCS_HIGHLAND, beam_mev=200.0, x0_mm=W.X0_WATER_MM)
+    else:
+        w = W.head_3d_spline(n_angles=7, paths_per_angle=333, n=(100, 100, 80), h=(2.0, 2.0, 2.0))
+        w["model"] = dict(w["model"], model=W.STRAIGHT_MCS, mcs=W.MCS_HIGHLAND, beam_mev=150.0)
+    g = run_gpu(pct, w, prec)
+    ref = run_oracle(orc, w)
+    st = compare(g, ref, exact_values=(prec == "f64"))
+    print(prec, case, st)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_area_raster_simulation(pct, orc, prec):
+    """A weighted-area phantom (Sec. II-A): x_true and the WEPL built on it."""
+    w = W.neo2_2d_spline(n_angles=12, paths_per_angle=200, n=200, h=1.0)
+    w["phantom"] = W.phantom(2, (200, 160), (1.0, 1.0), skin=True, raster=W.AREA, area_samples=6)
+    g = run_gpu(pct, w, prec)
+    ref = run_oracle(orc, w)
+    assert np.array_equal(to_np(g["x_true"]), ref["x_true"])
+    compare(g, ref, exact_values=(prec == "f64"))
 
 
 @pytest.mark.parametrize("prec", PRECS)
