@@ -55,14 +55,19 @@ enum { PCT_PATH_STRAIGHT = 0, PCT_PATH_STRAIGHT_MCS = 1, PCT_PATH_SPLINE = 2 };
 enum { PCT_CHORD_EXACT = 0, PCT_CHORD_CONSTANT = 1 };        /* Sec. II-C */
 enum { PCT_NOISE_NONE = 0, PCT_NOISE_GAUSS_REL = 1 };
 enum { PCT_MCS_FIXED = 0, PCT_MCS_HIGHLAND = 1 };            /* Sec. II-B exit widths */
-/* Arithmetic form of the path and traversal kernels.  Both give identical
+/* Arithmetic form of the path and traversal kernels.  All give identical
  * voxel indices and row pointers (every crossing decision equals the FP64
  * definition's); values and b agree within 1e-6 relative per row.
  *   PCT_PREC_MIXED: FP32 arithmetic with certified error bounds, exact FP64
  *                   evaluation only where a bound cannot decide; FP32 lengths,
  *                   FP32 Kahan-compensated WEPL.
- *   PCT_PREC_F64:   everything in FP64 (the comparison form).              */
-enum { PCT_PREC_MIXED = 0, PCT_PREC_F64 = 1 };
+ *   PCT_PREC_F64:   everything in FP64 (the comparison form).
+ *   PCT_PREC_MIXED_LEAN: PCT_PREC_MIXED with about a fifth of its workspace
+ *                   (the count keeps no per-segment records; the fill sets
+ *                   each row's segments up again), same bits as
+ *                   PCT_PREC_MIXED, slower fill: for systems whose workspace
+ *                   would not fit beside the CSR.                         */
+enum { PCT_PREC_MIXED = 0, PCT_PREC_F64 = 1, PCT_PREC_MIXED_LEAN = 2 };
 
 #define PCT_MAX_REGIONS 16
 #define PCT_MAX_SPLINE_SEGMENTS 1024
@@ -269,9 +274,10 @@ typedef struct {
 typedef struct pct_batch pct_batch; /* opaque */
 
 #define PCT_BATCH_AUTOTUNE 1 /* flags: time the launch shapes once and keep the fastest */
+#define PCT_BATCH_LEAN 2     /* flags: every item in the PCT_PREC_MIXED_LEAN form (small workspace) */
 
-/* bytes of device workspace pct_batch_create needs for these items */
-pct_status pct_batch_workspace_size(const pct_batch_item* items, int32_t n, size_t* bytes);
+/* bytes of device workspace pct_batch_create needs for these items and flags */
+pct_status pct_batch_workspace_size(const pct_batch_item* items, int32_t n, int32_t flags, size_t* bytes);
 
 /* Uploads every simulation's tables into the workspace, orders the work
  * items, optionally autotunes the launch shape (runs the count phase a few

@@ -146,7 +146,7 @@ struct Layout {
 
 pct_status check_geometry(const pct_phantom* ph, const pct_geometry* g, int precision) {
   if (!ph || !g) return fail(PCT_EINVAL, "NULL phantom or geometry");
-  if (precision != PCT_PREC_MIXED && precision != PCT_PREC_F64)
+  if (precision != PCT_PREC_MIXED && precision != PCT_PREC_F64 && precision != PCT_PREC_MIXED_LEAN)
     return fail(PCT_EINVAL, "bad precision %d", precision);
   if (g->n_angles < 0 || g->paths_per_angle < 0) return fail(PCT_EINVAL, "negative angle or path count");
   if (g->n_angles > 0 && !g->angles_rad) return fail(PCT_EINVAL, "angles_rad is NULL");
@@ -193,9 +193,9 @@ Layout layout_of(const pct_phantom* ph, const pct_geometry* g, int precision, lo
   L.args = off;
   off = align256(off + mixed_args_bytes());
   L.rec = off;
-  if (precision == PCT_PREC_MIXED)
+  if (precision != PCT_PREC_F64)
     off = align256(off + mixed_record_size(rec_rows >= 0 ? rec_rows : L.rows, ph ? ph->desc.dim : 3, g->model.model,
-                                           g->model.spline_segments));
+                                           g->model.spline_segments, precision == PCT_PREC_MIXED_LEAN));
   L.total = off;
   return L;
 }
@@ -310,7 +310,8 @@ extern "C" pct_status pct_simulate_count(const pct_phantom* ph, const pct_geomet
   if (precision == PCT_PREC_F64)
     launch_count_f64(S, 0, L.rows, rp + 1, st);
   else
-    launch_count_mixed(S, (const char*)ws + L.basis32, L.rows, (char*)ws + L.rec, rp + 1, (char*)ws + L.args, st);
+    launch_count_mixed(S, (const char*)ws + L.basis32, L.rows, (char*)ws + L.rec, rp + 1, (char*)ws + L.args, st,
+                       precision == PCT_PREC_MIXED_LEAN);
   if ((rc = cuda_check("count launch")) != PCT_OK) return rc;
   launch_scan_rowptr(rp, L.rows, (long long*)((char*)ws + L.partial), st);
   return cuda_check("scan launch");
@@ -330,7 +331,7 @@ extern "C" pct_status pct_simulate_fill(const pct_phantom* ph, const pct_geometr
     launch_fill_f64(S, 0, L.rows, rp, x, (int*)col, val, b, st);
   else
     launch_fill_mixed(S, (const char*)ws + L.basis32, L.rows, (const char*)ws + L.rec, rp, x, (int*)col, val, b,
-                      (char*)ws + L.args, st);
+                      (char*)ws + L.args, st, 0, -1, 0, true, precision == PCT_PREC_MIXED_LEAN);
   return cuda_check("fill launch");
 }
 
@@ -412,7 +413,7 @@ extern "C" pct_status pct_simulate_fill_host(const pct_phantom* ph, const pct_ge
     else
       launch_fill_mixed(S, (const char*)ws + L.basis32, L.rows, (const char*)ws + L.rec,
                         (const long long*)row_ptr_dev, x, col_s, val_s, b_s, (char*)ws + L.args, st, r0, r1, nz0,
-                        k == 0);
+                        k == 0, precision == PCT_PREC_MIXED_LEAN);
     ok = ok && cudaGetLastError() == cudaSuccess && cudaEventRecord(ev_fill[h], st) == cudaSuccess &&
          cudaStreamWaitEvent(cs, ev_fill[h], 0) == cudaSuccess;
     if (ok && nz1 > nz0)
@@ -538,7 +539,7 @@ pct_status project(bool adjoint, const pct_phantom* ph, const pct_geometry* g, c
       launch_mf_forward_f64(S, row0, n_rows, in, out, st);
   } else {
     launch_proj_mixed(adjoint, S, (const char*)ws + L.basis32, row0, n_rows, (char*)ws + L.rec, in, out,
-                      (char*)ws + L.args, st);
+                      (char*)ws + L.args, st, precision == PCT_PREC_MIXED_LEAN);
   }
   return cuda_check(what);
 }
@@ -572,6 +573,7 @@ struct pct_batch {
   unsigned long long* d_next = nullptr;   // two counters (2D, 3D launches)
   long long first3 = 0, total = 0;
   int grid_mult = 1, order_mode = 0;
+  bool lean = false;  // PCT_BATCH_LEAN: no segment records, fills rebuild the tables
   int bps[3][2] = {{1, 1}, {1, 1}, {1, 1}};  // resident blocks per SM [phase][dim 3]
   bool small[2] = {true, true};               // [dim 3]: every instance fits the smaller layout
   int sms = 1;
@@ -607,8 +609,9 @@ void batch_phase(pct_batch& b, bool fill, cudaStream_t st) {
   }
   // count: the FP64 path set-up, then the cooperative count; fill: the fill
   for (int f = fill ? 2 : 0; f <= (fill ? 2 : 1); ++f) {
-    launch_batch(f, 2, b.small[0], b.d_inst, b.n, 0, b.first3, b.d_next, b.sms * b.bps[f][0] * b.grid_mult, st);
-    launch_batch(f, 3, b.small[1], b.d_inst, b.n, b.first3, b.total, b.d_next + 1,
+    launch_batch(f, 2, b.small[0], b.lean, b.d_inst, b.n, 0, b.first3, b.d_next, b.sms * b.bps[f][0] * b.grid_mult,
+                 st);
+    launch_batch(f, 3, b.small[1], b.lean, b.d_inst, b.n, b.first3, b.total, b.d_next + 1,
                  b.sms * b.bps[f][1] * b.grid_mult, st);
   }
   if (!fill) {
@@ -646,13 +649,15 @@ pct_status batch_capture(pct_batch& b, bool fill) {
 
 }  // namespace
 
-extern "C" pct_status pct_batch_workspace_size(const pct_batch_item* items, int32_t n, size_t* bytes) {
+extern "C" pct_status pct_batch_workspace_size(const pct_batch_item* items, int32_t n, int32_t flags,
+                                                size_t* bytes) {
   if (!items || n < 1 || !bytes) return fail(PCT_EINVAL, "pct_batch_workspace_size: bad arguments");
+  const int form = (flags & PCT_BATCH_LEAN) ? PCT_PREC_MIXED_LEAN : PCT_PREC_MIXED;
   size_t off = 0;
   for (int k = 0; k < n; ++k) {
-    pct_status rc = check_geometry(items[k].phantom, &items[k].geo, PCT_PREC_MIXED);
+    pct_status rc = check_geometry(items[k].phantom, &items[k].geo, form);
     if (rc != PCT_OK) return rc;
-    off = align256(off + layout_of(items[k].phantom, &items[k].geo, PCT_PREC_MIXED).total);
+    off = align256(off + layout_of(items[k].phantom, &items[k].geo, form).total);
   }
   off = align256(off + sizeof(BatchInst) * (size_t)n);
   off = align256(off + 2 * sizeof(unsigned long long));
@@ -675,13 +680,15 @@ extern "C" pct_status pct_batch_create(const pct_batch_item* items, int32_t n, v
   if (!out) return fail(PCT_EINVAL, "pct_batch_create: out is NULL");
   *out = nullptr;
   size_t need = 0;
-  pct_status rc = pct_batch_workspace_size(items, n, &need);
+  pct_status rc = pct_batch_workspace_size(items, n, flags, &need);
+  const int form = (flags & PCT_BATCH_LEAN) ? PCT_PREC_MIXED_LEAN : PCT_PREC_MIXED;
   if (rc != PCT_OK) return rc;
   if (!ws || ws_bytes < need) return fail(PCT_ENOMEM, "batch workspace of %zu bytes is smaller than %zu", ws_bytes, need);
   cudaStream_t st = (cudaStream_t)stream;
   pct_batch* b = new (std::nothrow) pct_batch;
   if (!b) return fail(PCT_ENOMEM, "out of host memory");
   b->n = n;
+  b->lean = form == PCT_PREC_MIXED_LEAN;
   b->items.assign(items, items + n);
   b->layouts.resize(n);
   b->base.resize(n);
@@ -690,14 +697,14 @@ extern "C" pct_status pct_batch_create(const pct_batch_item* items, int32_t n, v
   size_t off = 0;
   for (int k = 0; k < n; ++k) {
     const pct_batch_item& it = items[k];
-    Layout L = layout_of(it.phantom, &it.geo, PCT_PREC_MIXED);
+    Layout L = layout_of(it.phantom, &it.geo, form);
     if (L.rows > 0 && (!it.row_ptr_dev || !it.x_true_dev)) {
       pct_batch_destroy(b);
       return fail(PCT_EINVAL, "batch item %d: NULL row_ptr_dev or x_true_dev", k);
     }
     b->base[k] = off;
     Layout L2;
-    rc = make_sim(it.phantom, &it.geo, PCT_PREC_MIXED, base + off, L.total, st, b->sims[k], L2);
+    rc = make_sim(it.phantom, &it.geo, form, base + off, L.total, st, b->sims[k], L2);
     if (rc != PCT_OK) {
       pct_batch_destroy(b);
       return rc;
@@ -718,7 +725,7 @@ extern "C" pct_status pct_batch_create(const pct_batch_item* items, int32_t n, v
     memset(&I, 0, sizeof(I));
     I.S = b->sims[k];
     I.M = mix_args(b->sims[k], b->layouts[k].rows, (const char*)b->sims[k].cs - b->layouts[k].cs + b->layouts[k].basis32,
-                   (char*)b->sims[k].cs - b->layouts[k].cs + b->layouts[k].rec);
+                   (char*)b->sims[k].cs - b->layouts[k].cs + b->layouts[k].rec, b->lean);
     I.n = b->layouts[k].rows;
     I.row_ptr_w = (long long*)items[k].row_ptr_dev;
     I.row_ptr = (const long long*)items[k].row_ptr_dev;
@@ -726,7 +733,7 @@ extern "C" pct_status pct_batch_create(const pct_batch_item* items, int32_t n, v
     if (!small_cap(I.M.seg_stride, I.S.ph.g)) b->small[I.S.ph.g.dim == 3 ? 1 : 0] = false;
   }
   for (int f = 0; f < 3; ++f)
-    for (int d = 0; d < 2; ++d) b->bps[f][d] = batch_blocks_per_sm(f, d == 0 ? 2 : 3, b->small[d]);
+    for (int d = 0; d < 2; ++d) b->bps[f][d] = batch_blocks_per_sm(f, d == 0 ? 2 : 3, b->small[d], b->lean);
   auto arrange = [&]() -> pct_status {
     std::vector<BatchInst> saved = by_item;
     pct_status r = PCT_OK;

@@ -288,9 +288,11 @@ struct CoopSmem {
 };
 
 // Fill: the records expanded into per-field arrays (no unpacking per crossing)
-template <int DIM, int CAP = kSegMax>
+template <int DIM, int CAP = kSegMax, bool LEAN = false>
 struct FillSmem {
   static constexpr int kCap = CAP;
+  static constexpr bool kLean = LEAN;
+  SegG<DIM> tab[LEAN ? CAP : 1];  // lean form: the row's segment table, rebuilt here
   static constexpr int kCross = CAP <= kSegSmall ? kRowCrossSmall : kRowCross;
   static constexpr int kQ = CAP <= kSegSmall ? kQueueSmall : kQueue;
   float4 ax[DIM][CAP];  // per axis: ph0, hv, 1 / hv, cb
@@ -435,8 +437,12 @@ static __device__ __noinline__ void walk_row_lane0(const SimDev* Sg, MixArgs M, 
     walk_row_df<DIM, false>(S, M, Sg, nullptr, r, p64, lane == 0, cs);
     if (lane == 0) {
       counts[row] = cs.n;
-      SegG<DIM>* rec = (SegG<DIM>*)M.segg + row * (long long)M.seg_stride;
-      reinterpret_cast<int*>(rec)[SegW<DIM>::MISC] = kRowIrregular;
+      if (M.rflag) {
+        M.rflag[row] = 1;  // lean form: the row flag
+      } else {
+        SegG<DIM>* rec = (SegG<DIM>*)M.segg + row * (long long)M.seg_stride;
+        reinterpret_cast<int*>(rec)[SegW<DIM>::MISC] = kRowIrregular;
+      }
     }
   }
   __syncwarp();
@@ -818,6 +824,108 @@ __device__ __forceinline__ void fill_axis(SM& sm, int nseg, int lane, const SimD
 // exact ties between crossings of different axes, writes the compact
 // segment records and the row's entry count.
 // ---------------------------------------------------------------------------
+// Steps 1-2 of the count, shared with the lean fill: the row's segment table
+// in tab[0..nseg) -- lead segments from the path kernel, interior ones set up
+// here (one per lane) -- with each segment's merge bit, first CSR slot within
+// the row and merged tail.  *totE receives the row's entry count.  Returns
+// false where the cooperative form cannot take the row (a segment it cannot
+// set up, more than kCross crossings).
+template <int DIM, int kCross>
+__device__ __forceinline__ bool row_table(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
+                                          long long row, int nseg, SegG<DIM>* tab, int* totE) {
+  using W = SegW<DIM>;
+  const int lane = threadIdx.x & 31;
+  const GridDev& g = S.ph.g;
+  const RowDF& r = M.rdf[row];
+  const int stride[3] = {1, g.n[0], g.n[0] * (DIM > 2 ? g.n[1] : 1)};
+  const PathF64* p64 = M.r64 + row;
+  // 1. segment table: lead segments from the pre-pass, interior ones here
+  const SegP<DIM>* lead = lead_rec<DIM>(M, row);
+  if (lane < 2 && (lane == 0 || nseg > 1)) {
+    const SegP<DIM> p = lead[lane];
+    const int s = lane == 0 ? 0 : nseg - 1;
+    store_rec<DIM>(tab[s], pack_seg<DIM>(p));
+  }
+  const int nint = nseg - 2;
+  const float mag = r.mag;
+  for (int base = 0; base < nint; base += 32) {
+    const int j = base + lane;
+    df V[3], Vn[3];
+    if (j <= nint) vertex_df<DIM>(r, M.tab, M.R, 1 + j, V);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      Vn[a].hi = __shfl_down_sync(0xffffffffu, V[a].hi, 1);
+      Vn[a].lo = __shfl_down_sync(0xffffffffu, V[a].lo, 1);
+    }
+    if (lane == 31 && j < nint) vertex_df<DIM>(r, M.tab, M.R, 2 + j, Vn);
+    if (j < nint) {
+      const SegP<DIM> p = seg_prepare<DIM>(g, M.gd, Sg, gdg, V, Vn, mag, ExactRef{Sg, p64, 1 + j});
+      store_rec<DIM>(tab[1 + j], pack_seg<DIM>(p));
+    }
+  }
+  __syncwarp();
+
+  // 2. per-segment crossings, merges, entries; prefix sums
+  int bad = 0, merge[2] = {0, 0}, Cs[2] = {0, 0}, Es[2] = {0, 0};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int s = lane + 32 * h;
+    if (s < nseg) {
+      const SegR<DIM> R = load_seg<DIM>(tab[s]);
+      const int st = R.w[W::MISC] & 3;
+      int m = 0;
+      if (s > 0 && st == kStRegular) {
+        const SegR<DIM> Q = load_seg<DIM>(tab[s - 1]);
+        if ((Q.w[W::MISC] & 3) == kStRegular) {
+          int colx = Q.w[W::COL0];
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) colx += Q.cnt(a) * dcol_of<DIM>(stride, Q.w[W::MISC], a);
+          m = colx == R.w[W::COL0];
+        }
+      }
+      Cs[h] = R.C();
+      Es[h] = (st == kStRegular) ? Cs[h] + 1 - m : 0;
+      merge[h] = m;
+      bad |= st == kStIrregular;
+    }
+  }
+  int t0, t1, eb[2];
+  const int totC = __reduce_add_sync(0xffffffffu, Cs[0] + Cs[1]);
+  eb[0] = warp_excl_scan(Es[0], lane, &t0);
+  eb[1] = warp_excl_scan(Es[1], lane, &t1) + t0;
+  *totE = t0 + t1;
+  bad |= totC > kCross;
+  const bool irregular = __any_sync(0xffffffffu, bad) != 0;
+  __syncwarp();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int s = lane + 32 * h;
+    if (s < nseg) {
+      int* ws = reinterpret_cast<int*>(&tab[s]);
+      if (merge[h]) ws[W::MISC] |= kMergeBit;
+      ws[W::EBASE] = eb[h];
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int s = lane + 32 * h;
+    if (s < nseg) {
+      float t = 0.f;
+      for (int u = s + 1; u < nseg; ++u) {
+        const int* wu = reinterpret_cast<const int*>(&tab[u]);
+        if (!(wu[W::MISC] & kMergeBit)) break;
+        t = t + __int_as_float(wu[W::FIRST]);
+        const int c01 = wu[W::CNT];
+        if ((c01 & 0xffff) + ((unsigned)c01 >> 16) + (DIM > 2 ? wu[W::CNT + 1] & 0xffff : 0) > 0) break;
+      }
+      reinterpret_cast<int*>(&tab[s])[W::TAIL] = __float_as_int(t);
+    }
+  }
+  __syncwarp();
+  return !irregular;
+}
+
 template <int DIM, class SM>
 __device__ __forceinline__ bool coop_count_row(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
                                                long long row, SM& sm, long long* __restrict__ counts) {
@@ -830,90 +938,8 @@ __device__ __forceinline__ bool coop_count_row(const SimDev& S, const MixArgs& M
   const PathF64* p64 = M.r64 + row;
   bool irregular = nseg > SM::kCap || nseg < 1 || nseg > M.seg_stride;
   if (!irregular) {
-    // 1. segment table: lead segments from the pre-pass, interior ones here
-    const SegP<DIM>* lead = lead_rec<DIM>(M, row);
-    if (lane < 2 && (lane == 0 || nseg > 1)) {
-      const SegP<DIM> p = lead[lane];
-      const int s = lane == 0 ? 0 : nseg - 1;
-      store_rec<DIM>(sm.tab[s], pack_seg<DIM>(p));
-    }
-    const int nint = nseg - 2;
-    const float mag = r.mag;
-    for (int base = 0; base < nint; base += 32) {
-      const int j = base + lane;
-      df V[3], Vn[3];
-      if (j <= nint) vertex_df<DIM>(r, M.tab, M.R, 1 + j, V);
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        Vn[a].hi = __shfl_down_sync(0xffffffffu, V[a].hi, 1);
-        Vn[a].lo = __shfl_down_sync(0xffffffffu, V[a].lo, 1);
-      }
-      if (lane == 31 && j < nint) vertex_df<DIM>(r, M.tab, M.R, 2 + j, Vn);
-      if (j < nint) {
-        const SegP<DIM> p = seg_prepare<DIM>(g, M.gd, Sg, gdg, V, Vn, mag, ExactRef{Sg, p64, 1 + j});
-        store_rec<DIM>(sm.tab[1 + j], pack_seg<DIM>(p));
-      }
-    }
-    __syncwarp();
-
-    // 2. per-segment crossings, merges, entries; prefix sums
-    int bad = 0, merge[2] = {0, 0}, Cs[2] = {0, 0}, Es[2] = {0, 0};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int s = lane + 32 * h;
-      if (s < nseg) {
-        const SegR<DIM> R = load_seg<DIM>(sm.tab[s]);
-        const int st = R.w[W::MISC] & 3;
-        int m = 0;
-        if (s > 0 && st == kStRegular) {
-          const SegR<DIM> Q = load_seg<DIM>(sm.tab[s - 1]);
-          if ((Q.w[W::MISC] & 3) == kStRegular) {
-            int colx = Q.w[W::COL0];
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) colx += Q.cnt(a) * dcol_of<DIM>(stride, Q.w[W::MISC], a);
-            m = colx == R.w[W::COL0];
-          }
-        }
-        Cs[h] = R.C();
-        Es[h] = (st == kStRegular) ? Cs[h] + 1 - m : 0;
-        merge[h] = m;
-        bad |= st == kStIrregular;
-      }
-    }
-    int t0, t1, eb[2];
-    const int totC = __reduce_add_sync(0xffffffffu, Cs[0] + Cs[1]);
-    eb[0] = warp_excl_scan(Es[0], lane, &t0);
-    eb[1] = warp_excl_scan(Es[1], lane, &t1) + t0;
-    const int totE = t0 + t1;
-    bad |= totC > SM::kCross;
-    irregular = __any_sync(0xffffffffu, bad) != 0;
-    __syncwarp();
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int s = lane + 32 * h;
-      if (s < nseg) {
-        int* ws = reinterpret_cast<int*>(&sm.tab[s]);
-        if (merge[h]) ws[W::MISC] |= kMergeBit;
-        ws[W::EBASE] = eb[h];
-      }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int s = lane + 32 * h;
-      if (s < nseg) {
-        float t = 0.f;
-        for (int u = s + 1; u < nseg; ++u) {
-          const int* wu = reinterpret_cast<const int*>(&sm.tab[u]);
-          if (!(wu[W::MISC] & kMergeBit)) break;
-          t = t + __int_as_float(wu[W::FIRST]);
-          const int c01 = wu[W::CNT];
-          if ((c01 & 0xffff) + ((unsigned)c01 >> 16) + (DIM > 2 ? wu[W::CNT + 1] & 0xffff : 0) > 0) break;
-        }
-        reinterpret_cast<int*>(&sm.tab[s])[W::TAIL] = __float_as_int(t);
-      }
-    }
-    __syncwarp();
+    int totE = 0;
+    irregular = !row_table<DIM, SM::kCross>(S, M, Sg, gdg, row, nseg, sm.tab, &totE);
 
     // 3. exact ties between crossings of different axes (each crossing of
     // axis a >= 1 against the nearest planes of the axes below it)
@@ -924,10 +950,15 @@ __device__ __forceinline__ bool coop_count_row(const SimDev& S, const MixArgs& M
       irregular = __any_sync(0xffffffffu, tie || overflow) != 0;
     }
     if (!irregular) {
-      SegG<DIM>* dst = (SegG<DIM>*)M.segg + row * (long long)M.seg_stride;
-      const int4* src = reinterpret_cast<const int4*>(sm.tab);
-      int4* d4 = reinterpret_cast<int4*>(dst);
-      for (int q = lane; q < nseg * W::NV; q += 32) d4[q] = src[q];
+      if (M.rflag) {
+        // lean form: no segment records, the fill rebuilds the table
+        if (lane == 0) M.rflag[row] = 0;
+      } else {
+        SegG<DIM>* dst = (SegG<DIM>*)M.segg + row * (long long)M.seg_stride;
+        const int4* src = reinterpret_cast<const int4*>(sm.tab);
+        int4* d4 = reinterpret_cast<int4*>(dst);
+        for (int q = lane; q < nseg * W::NV; q += 32) d4[q] = src[q];
+      }
       if (lane == 0) counts[row] = totE;
       __syncwarp();
       return true;
@@ -953,8 +984,8 @@ __device__ __forceinline__ void count_row_walk(const SimDev* Sg, const MixArgs& 
 // its CSR position; entry 0 of every segment comes from the segment's lane.
 // ---------------------------------------------------------------------------
 template <int DIM, class SM>
-__device__ __forceinline__ bool coop_fill_row(const SimDev& S, const MixArgs& M, const SimDev* Sg, long long row,
-                                              SM& sm, const long long* __restrict__ row_ptr,
+__device__ __forceinline__ bool coop_fill_row(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
+                                              long long row, SM& sm, const long long* __restrict__ row_ptr,
                                               const float* __restrict__ x, int* __restrict__ col,
                                               float* __restrict__ val, float* __restrict__ b) {
   using W = SegW<DIM>;
@@ -963,9 +994,21 @@ __device__ __forceinline__ bool coop_fill_row(const SimDev& S, const MixArgs& M,
   const RowDF& r = M.rdf[row];
   const int nseg = r.nv - 1;
   const long long rowstart = row_ptr[row], rowend = row_ptr[row + 1];
-  const SegG<DIM>* rec = (const SegG<DIM>*)M.segg + row * (long long)M.seg_stride;
+  const SegG<DIM>* rec;
   bool irregular = nseg > SM::kCap || nseg < 1 || nseg > M.seg_stride;
-  if (!irregular) irregular = (reinterpret_cast<const int*>(rec)[W::MISC] & kRowIrregular) != 0;
+  if constexpr (SM::kLean) {
+    // lean form: the count left only the row flag; the segment table is
+    // rebuilt in shared memory by the count's own code (same records)
+    rec = sm.tab;
+    if (!irregular) irregular = M.rflag[row] != 0;
+    if (!irregular) {
+      int totE;
+      row_table<DIM, SM::kCross>(S, M, Sg, gdg, row, nseg, sm.tab, &totE);
+    }
+  } else {
+    rec = (const SegG<DIM>*)M.segg + row * (long long)M.seg_stride;
+    if (!irregular) irregular = (reinterpret_cast<const int*>(rec)[W::MISC] & kRowIrregular) != 0;
+  }
   if (!irregular) {
     const int stride[3] = {1, g.n[0], g.n[0] * (DIM > 2 ? g.n[1] : 1)};
     // 1. the row's records, expanded: one segment per lane

@@ -25,9 +25,9 @@ __device__ __forceinline__ SM& warp_smem() {
 
 // dynamic shared memory of a 128-thread count / fill block (rows of up to
 // CAP segments)
-template <int DIM, bool kFill, int CAP>
+template <int DIM, bool kFill, int CAP, bool LEAN = false>
 constexpr size_t coop_bytes() {
-  return kFill ? 4 * sizeof(FillSmem<DIM, CAP>) : 4 * sizeof(CoopSmem<DIM, CAP>);
+  return kFill ? 4 * sizeof(FillSmem<DIM, CAP, LEAN>) : 4 * sizeof(CoopSmem<DIM, CAP>);
 }
 
 // the smaller layout: rows of up to kSegSmall segments on grids whose
@@ -116,12 +116,12 @@ __global__ void __launch_bounds__(128, 8) k_count_mixed(SimDev S, MixArgs M, con
 
 // One block of 128 consecutive rows starting at row0 (fill phase): each
 // warp writes one row at a time.
-template <int DIM, int CAP>
+template <int DIM, int CAP, bool LEAN>
 __device__ __forceinline__ void fill_block(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
                                            long long n, long long row0, const long long* __restrict__ row_ptr,
                                            const float* __restrict__ x, int* __restrict__ col,
                                            float* __restrict__ val, float* __restrict__ b) {
-  FillSmem<DIM, CAP>& sm = warp_smem<FillSmem<DIM, CAP>>();
+  FillSmem<DIM, CAP, LEAN>& sm = warp_smem<FillSmem<DIM, CAP, LEAN>>();
   const int lane = threadIdx.x & 31;
   const int lines = (M.seg_stride * (int)sizeof(SegG<DIM>) + 127) / 128;
   __shared__ int take, n_walk;
@@ -136,13 +136,13 @@ __device__ __forceinline__ void fill_block(const SimDev& S, const MixArgs& M, co
     const long long row = row0 + k;
     const int kn = next_row_of_block(&take);
     // the next row's segment records into L2 while this row is written
-    if (kn < 128 && row0 + kn < n) {
+    if (!LEAN && kn < 128 && row0 + kn < n) {
       const long long rn = row0 + kn;
       const char* nx = (const char*)((const SegG<DIM>*)M.segg + rn * (long long)M.seg_stride);
       if (lane < lines) asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + 128 * lane));
       if (lane == 31) asm volatile("prefetch.global.L2 [%0];" ::"l"(M.rdf + rn));
     }
-    if (!coop_fill_row<DIM>(S, M, Sg, row, sm, row_ptr, x, col, val, b) && lane == 0)
+    if (!coop_fill_row<DIM>(S, M, Sg, gdg, row, sm, row_ptr, x, col, val, b) && lane == 0)
       walk[atomicAdd(&n_walk, 1)] = (unsigned char)k;
     k = kn;
   }
@@ -159,24 +159,24 @@ constexpr int fill_blocks_per_sm() {
   return DIM == 3 ? 8 : 7;
 }
 
-template <int DIM, int CAP>
+template <int DIM, int CAP, bool LEAN>
 __global__ void __launch_bounds__(128, fill_blocks_per_sm<DIM>()) k_fill_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
                                                     long long n, const long long* __restrict__ row_ptr,
                                                     const float* __restrict__ x, int* __restrict__ col,
                                                     float* __restrict__ val, float* __restrict__ b) {
-  fill_block<DIM, CAP>(S, M, Sg, gdg, n, (long long)blockIdx.x * blockDim.x, row_ptr, x, col, val, b);
+  fill_block<DIM, CAP, LEAN>(S, M, Sg, gdg, n, (long long)blockIdx.x * blockDim.x, row_ptr, x, col, val, b);
 }
 
 // rows [row_begin, n) only (a kernel of its own, so that the whole fill
 // keeps its first row at compile-time zero)
-template <int DIM, int CAP>
+template <int DIM, int CAP, bool LEAN>
 __global__ void __launch_bounds__(128, fill_blocks_per_sm<DIM>()) k_fill_mixed_range(SimDev S, MixArgs M, const SimDev* Sg,
                                                           const GridDF* gdg, long long n,
                                                           const long long* __restrict__ row_ptr,
                                                           const float* __restrict__ x, int* __restrict__ col,
                                                           float* __restrict__ val, float* __restrict__ b,
                                                           long long row_begin) {
-  fill_block<DIM, CAP>(S, M, Sg, gdg, n, row_begin + (long long)blockIdx.x * blockDim.x, row_ptr, x, col, val, b);
+  fill_block<DIM, CAP, LEAN>(S, M, Sg, gdg, n, row_begin + (long long)blockIdx.x * blockDim.x, row_ptr, x, col, val, b);
 }
 
 // ---------------------------------------------------------------------------
@@ -198,7 +198,7 @@ __device__ __forceinline__ int batch_find(const BatchInst* __restrict__ B, int n
 
 // phases: 0 path set-up, 1 count, 2 fill (the launch bounds follow the
 // per-simulation kernels of each phase)
-template <int kPhase, int DIM, int CAP>
+template <int kPhase, int DIM, int CAP, bool LEAN>
 __global__ void __launch_bounds__(128, kPhase == 0 ? 1 : (kPhase == 1 ? 8 : fill_blocks_per_sm<DIM>()))
     k_batch(const BatchInst* __restrict__ B, int n_inst, long long first, long long last,
             unsigned long long* next) {
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(128, kPhase == 0 ? 1 : (kPhase == 1 ? 8 : fill
     const BatchInst& I = B[batch_find(B, n_inst, item)];
     const long long row0 = (item - I.item0) * 128;
     if constexpr (kPhase == 2)
-      fill_block<DIM, CAP>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, I.row_ptr, I.x, I.col, I.val, I.b);
+      fill_block<DIM, CAP, LEAN>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, I.row_ptr, I.x, I.col, I.val, I.b);
     else if constexpr (kPhase == 1)
       rows_block<DIM, CAP>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, I.row_ptr_w + 1);
     else
@@ -226,56 +226,70 @@ static void smem_attr(Kern k, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int kPhase, int DIM, int CAP>
+template <int kPhase, int DIM, int CAP, bool LEAN>
 static size_t batch_smem() {
-  return kPhase == 0 ? 0 : coop_bytes<DIM, kPhase == 2, CAP>();
+  return kPhase == 0 ? 0 : coop_bytes<DIM, kPhase == 2, CAP, LEAN>();
 }
 
-template <int kPhase, int DIM, int CAP>
+template <int kPhase, int DIM, int CAP, bool LEAN = false>
 static int blocks_per_sm() {
   int nb = 0;
-  smem_attr(k_batch<kPhase, DIM, CAP>, batch_smem<kPhase, DIM, CAP>());
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<kPhase, DIM, CAP>, 128, batch_smem<kPhase, DIM, CAP>());
+  smem_attr(k_batch<kPhase, DIM, CAP, LEAN>, batch_smem<kPhase, DIM, CAP, LEAN>());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<kPhase, DIM, CAP, LEAN>, 128,
+                                                batch_smem<kPhase, DIM, CAP, LEAN>());
   return nb > 0 ? nb : 1;
 }
 
 // (the path phase has no shared memory: one capacity serves every batch)
-int batch_blocks_per_sm(int phase, int dim, bool small) {
+// (the path phase has no shared memory: one capacity serves every batch;
+// the count phase reads the lean flag from each instance's arguments)
+int batch_blocks_per_sm(int phase, int dim, bool small, bool lean) {
   if (phase == 0) return dim == 2 ? blocks_per_sm<0, 2, kSegMax>() : blocks_per_sm<0, 3, kSegMax>();
   if (phase == 1) {
     if (small) return dim == 2 ? blocks_per_sm<1, 2, kSegSmall>() : blocks_per_sm<1, 3, kSegSmall>();
     return dim == 2 ? blocks_per_sm<1, 2, kSegMax>() : blocks_per_sm<1, 3, kSegMax>();
   }
+  if (lean) {
+    if (small) return dim == 2 ? blocks_per_sm<2, 2, kSegSmall, true>() : blocks_per_sm<2, 3, kSegSmall, true>();
+    return dim == 2 ? blocks_per_sm<2, 2, kSegMax, true>() : blocks_per_sm<2, 3, kSegMax, true>();
+  }
   if (small) return dim == 2 ? blocks_per_sm<2, 2, kSegSmall>() : blocks_per_sm<2, 3, kSegSmall>();
   return dim == 2 ? blocks_per_sm<2, 2, kSegMax>() : blocks_per_sm<2, 3, kSegMax>();
 }
 
-template <int kPhase, int DIM, int CAP>
+template <int kPhase, int DIM, int CAP, bool LEAN>
 static void launch_phase(const BatchInst* B, int n_inst, long long first, long long last, unsigned long long* next,
                          int grid, cudaStream_t st) {
-  smem_attr(k_batch<kPhase, DIM, CAP>, batch_smem<kPhase, DIM, CAP>());
-  k_batch<kPhase, DIM, CAP><<<grid, 128, batch_smem<kPhase, DIM, CAP>(), st>>>(B, n_inst, first, last, next);
+  smem_attr(k_batch<kPhase, DIM, CAP, LEAN>, batch_smem<kPhase, DIM, CAP, LEAN>());
+  k_batch<kPhase, DIM, CAP, LEAN><<<grid, 128, batch_smem<kPhase, DIM, CAP, LEAN>(), st>>>(B, n_inst, first, last,
+                                                                                          next);
 }
 
 template <int kPhase, int DIM>
-static void launch_phase_cap(bool small, const BatchInst* B, int n_inst, long long first, long long last,
+static void launch_phase_cap(bool small, bool lean, const BatchInst* B, int n_inst, long long first, long long last,
                              unsigned long long* next, int grid, cudaStream_t st) {
-  if (kPhase == 0 || !small)
-    launch_phase<kPhase, DIM, kSegMax>(B, n_inst, first, last, next, grid, st);
-  else
-    launch_phase<kPhase, DIM, kSegSmall>(B, n_inst, first, last, next, grid, st);
+  if (kPhase == 2 && lean) {
+    if (small)
+      launch_phase<kPhase, DIM, kSegSmall, true>(B, n_inst, first, last, next, grid, st);
+    else
+      launch_phase<kPhase, DIM, kSegMax, true>(B, n_inst, first, last, next, grid, st);
+  } else if (kPhase == 0 || !small) {
+    launch_phase<kPhase, DIM, kSegMax, false>(B, n_inst, first, last, next, grid, st);
+  } else {
+    launch_phase<kPhase, DIM, kSegSmall, false>(B, n_inst, first, last, next, grid, st);
+  }
 }
 
-void launch_batch(int phase, int dim, bool small, const BatchInst* B, int n_inst, long long first, long long last,
-                  unsigned long long* next, int grid, cudaStream_t st) {
+void launch_batch(int phase, int dim, bool small, bool lean, const BatchInst* B, int n_inst, long long first,
+                  long long last, unsigned long long* next, int grid, cudaStream_t st) {
   cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
   if (last <= first || n_inst <= 0) return;
-  if (phase == 0 && dim == 2) launch_phase_cap<0, 2>(small, B, n_inst, first, last, next, grid, st);
-  if (phase == 0 && dim == 3) launch_phase_cap<0, 3>(small, B, n_inst, first, last, next, grid, st);
-  if (phase == 1 && dim == 2) launch_phase_cap<1, 2>(small, B, n_inst, first, last, next, grid, st);
-  if (phase == 1 && dim == 3) launch_phase_cap<1, 3>(small, B, n_inst, first, last, next, grid, st);
-  if (phase == 2 && dim == 2) launch_phase_cap<2, 2>(small, B, n_inst, first, last, next, grid, st);
-  if (phase == 2 && dim == 3) launch_phase_cap<2, 3>(small, B, n_inst, first, last, next, grid, st);
+  if (phase == 0 && dim == 2) launch_phase_cap<0, 2>(small, lean, B, n_inst, first, last, next, grid, st);
+  if (phase == 0 && dim == 3) launch_phase_cap<0, 3>(small, lean, B, n_inst, first, last, next, grid, st);
+  if (phase == 1 && dim == 2) launch_phase_cap<1, 2>(small, lean, B, n_inst, first, last, next, grid, st);
+  if (phase == 1 && dim == 3) launch_phase_cap<1, 3>(small, lean, B, n_inst, first, last, next, grid, st);
+  if (phase == 2 && dim == 2) launch_phase_cap<2, 2>(small, lean, B, n_inst, first, last, next, grid, st);
+  if (phase == 2 && dim == 3) launch_phase_cap<2, 3>(small, lean, B, n_inst, first, last, next, grid, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -350,7 +364,7 @@ static df split_host(double v) {
   return df{hi, (float)(v - (double)hi)};
 }
 
-MixArgs mix_args(const SimDev& S, long long n, const void* tab, void* rec) {
+MixArgs mix_args(const SimDev& S, long long n, const void* tab, void* rec, bool lean) {
   MixArgs M;
   for (int a = 0; a < 3; ++a) {
     M.gd.o[a] = split_host(S.ph.g.o[a]);
@@ -367,7 +381,8 @@ MixArgs mix_args(const SimDev& S, long long n, const void* tab, void* rec) {
   M.rdf = (RowDF*)rec;
   M.r64 = (PathF64*)((char*)rec + o64);
   M.lead = (char*)rec + olead;
-  M.segg = (char*)rec + osegg;
+  M.segg = lean ? nullptr : (char*)rec + osegg;
+  M.rflag = lean ? (unsigned char*)rec + osegg : nullptr;  // (the segment records' place)
   M.seg_stride = seg_stride_of(S.md.model, S.md.K);
   return M;
 }
@@ -416,25 +431,39 @@ static void launch_count_cap(bool small, unsigned blocks, const SimDev& S, const
   }
 }
 
+template <int DIM, int CAP, bool LEAN>
+static void launch_fill_lean(bool whole, unsigned blocks, const SimDev& S, const MixArgs& M, const SimDev* Sg,
+                             const GridDF* gdg, long long n, long long row_end, long long row_begin,
+                             const long long* row_ptr, const float* x, int* col, float* val, float* b,
+                             cudaStream_t st) {
+  const size_t sm = coop_bytes<DIM, true, CAP, LEAN>();
+  if (whole) {
+    smem_attr(k_fill_mixed<DIM, CAP, LEAN>, sm);
+    k_fill_mixed<DIM, CAP, LEAN><<<blocks, 128, sm, st>>>(S, M, Sg, gdg, n, row_ptr, x, col, val, b);
+  } else {
+    smem_attr(k_fill_mixed_range<DIM, CAP, LEAN>, sm);
+    k_fill_mixed_range<DIM, CAP, LEAN><<<blocks, 128, sm, st>>>(S, M, Sg, gdg, row_end, row_ptr, x, col, val, b,
+                                                                 row_begin);
+  }
+}
+
 template <int DIM, int CAP>
 static void launch_fill_cap(bool whole, unsigned blocks, const SimDev& S, const MixArgs& M, const SimDev* Sg,
                             const GridDF* gdg, long long n, long long row_end, long long row_begin,
                             const long long* row_ptr, const float* x, int* col, float* val, float* b,
                             cudaStream_t st) {
-  const size_t sm = coop_bytes<DIM, true, CAP>();
-  if (whole) {
-    smem_attr(k_fill_mixed<DIM, CAP>, sm);
-    k_fill_mixed<DIM, CAP><<<blocks, 128, sm, st>>>(S, M, Sg, gdg, n, row_ptr, x, col, val, b);
-  } else {
-    smem_attr(k_fill_mixed_range<DIM, CAP>, sm);
-    k_fill_mixed_range<DIM, CAP><<<blocks, 128, sm, st>>>(S, M, Sg, gdg, row_end, row_ptr, x, col, val, b, row_begin);
-  }
+  if (M.rflag)
+    launch_fill_lean<DIM, CAP, true>(whole, blocks, S, M, Sg, gdg, n, row_end, row_begin, row_ptr, x, col, val, b,
+                                     st);
+  else
+    launch_fill_lean<DIM, CAP, false>(whole, blocks, S, M, Sg, gdg, n, row_end, row_begin, row_ptr, x, col, val, b,
+                                      st);
 }
 
 void launch_count_mixed(const SimDev& S, const void* tab, long long n, void* rec, long long* counts, void* args,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool lean) {
   if (n <= 0) return;
-  MixArgs M = mix_args(S, n, tab, rec);
+  MixArgs M = mix_args(S, n, tab, rec, lean);
   const SimDev* Sg;
   const GridDF* gdg;
   if (!upload_args(S, M, args, st, &Sg, &gdg)) return;
@@ -452,10 +481,10 @@ void launch_count_mixed(const SimDev& S, const void* tab, long long n, void* rec
 
 void launch_fill_mixed(const SimDev& S, const void* tab, long long n, const void* rec, const long long* row_ptr,
                        const float* x, int* col, float* val, float* b, void* args, cudaStream_t st,
-                       long long row_begin, long long row_end, long long nz0, bool upload) {
+                       long long row_begin, long long row_end, long long nz0, bool upload, bool lean) {
   if (row_end < 0) row_end = n;
   if (n <= 0 || row_end <= row_begin) return;
-  MixArgs M = mix_args(S, n, tab, (void*)rec);
+  MixArgs M = mix_args(S, n, tab, (void*)rec, lean);
   const SimDev* Sg;
   const GridDF* gdg;
   if (upload) {
@@ -488,9 +517,9 @@ void launch_fill_mixed(const SimDev& S, const void* tab, long long n, const void
 }
 
 void launch_proj_mixed(bool adjoint, const SimDev& S, const void* tab, long long row_base, long long n, void* rec,
-                       const float* in, float* out, void* args, cudaStream_t st) {
+                       const float* in, float* out, void* args, cudaStream_t st, bool lean) {
   if (n <= 0) return;
-  MixArgs M = mix_args(S, n, tab, rec);
+  MixArgs M = mix_args(S, n, tab, rec, lean);
   const SimDev* Sg;
   const GridDF* gdg;
   if (!upload_args(S, M, args, st, &Sg, &gdg)) return;
@@ -514,11 +543,13 @@ int seg_stride_of(int model, int K) {
   return nseg < 1 ? 1 : (nseg > kSegMax ? kSegMax : nseg);
 }
 
-size_t mixed_record_size(long long rows, int dim, int model, int K) {
+size_t mixed_record_size(long long rows, int dim, int model, int K, bool lean) {
   size_t r = (size_t)(rows > 0 ? rows : 1);
   const size_t seg = dim == 3 ? sizeof(SegG<3>) : sizeof(SegG<2>);
+  // lean form: one flag byte per row in place of the segment records
+  const size_t last = lean ? r : r * (size_t)seg_stride_of(model, K) * seg;
   return ((r * sizeof(RowDF) + 255) & ~(size_t)255) + ((r * sizeof(PathF64) + 255) & ~(size_t)255) +
-         ((2 * r * sizeof(SegP<3>) + 255) & ~(size_t)255) + r * (size_t)seg_stride_of(model, K) * seg + 256;
+         ((2 * r * sizeof(SegP<3>) + 255) & ~(size_t)255) + last + 256;
 }
 
 }  // namespace pct

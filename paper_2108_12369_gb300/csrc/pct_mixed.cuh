@@ -652,7 +652,8 @@ struct MixArgs {
   RowDF* rdf;           // [rows]
   PathF64* r64;         // [rows]
   void* lead;           // [rows][2] summaries of the lead-in / lead-out segments
-  void* segg;           // [rows][seg_stride] compact segment records (count -> fill)
+  void* segg;           // [rows][seg_stride] compact segment records (count -> fill); NULL in the lean form
+  unsigned char* rflag; // lean form: [rows] 1 = the row goes to the per-lane walker; NULL otherwise
   int seg_stride;
 };
 
@@ -671,15 +672,15 @@ struct BatchInst {
   float* b;
 };
 
-MixArgs mix_args(const SimDev& S, long long n, const void* tab, void* rec);
+MixArgs mix_args(const SimDev& S, long long n, const void* tab, void* rec, bool lean = false);
 // persistent launch of one phase (0 path set-up, 1 count, 2 fill) over the
 // items [first, last) (all of dimension dim)
 // whether a simulation (rows of up to seg_stride segments, grid g) takes the
 // smaller per-warp shared-memory layout of the count / fill kernels
 bool small_cap(int seg_stride, const GridDev& g);
 // small: every instance of that dimension fits the smaller layout
-int batch_blocks_per_sm(int phase, int dim, bool small);
-void launch_batch(int phase, int dim, bool small, const BatchInst* B, int n_inst, long long first, long long last,
-                  unsigned long long* next, int grid, cudaStream_t st);
+int batch_blocks_per_sm(int phase, int dim, bool small, bool lean = false);
+void launch_batch(int phase, int dim, bool small, bool lean, const BatchInst* B, int n_inst, long long first,
+                  long long last, unsigned long long* next, int grid, cudaStream_t st);
 
 }  // namespace pct

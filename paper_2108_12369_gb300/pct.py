@@ -16,7 +16,7 @@ from . import workloads as W
 LIB_PATH = Path(__file__).resolve().parent / "_build" / "libpct.so"
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
-PREC_MIXED, PREC_F64 = 0, 1
+PREC_MIXED, PREC_F64, PREC_MIXED_LEAN = 0, 1, 2
 MAX_REGIONS = 16
 
 
@@ -72,7 +72,7 @@ EXPORTS = ["pct_phantom_create", "pct_phantom_destroy", "pct_phantom_nvox", "pct
            "pct_batch_count", "pct_batch_nnz", "pct_batch_fill", "pct_batch_params", "pct_batch_destroy",
            "pct_scan_counts_static", "pct_sap_workspace_size", "pct_sap", "pct_csr_file_create",
            "pct_csr_file_write_rows", "pct_last_error", "pct_version"]
-BATCH_AUTOTUNE = 1
+BATCH_AUTOTUNE, BATCH_LEAN = 1, 2
 STATIC_SCAN_MAX_ROWS = 1 << 28
 
 _lib = None
@@ -105,7 +105,7 @@ def lib():
             "pct_adjoint": ([vp, P(Geometry), P(Csr), C.c_int32, C.c_int64, C.c_int64, vp, vp, vp,
                              C.c_size_t, vp], C.c_int),
             "pct_scan_counts_static": ([vp, C.c_int64, vp], C.c_int),
-            "pct_batch_workspace_size": ([P(BatchItem), C.c_int32, P(C.c_size_t)], C.c_int),
+            "pct_batch_workspace_size": ([P(BatchItem), C.c_int32, C.c_int32, P(C.c_size_t)], C.c_int),
             "pct_batch_create": ([P(BatchItem), C.c_int32, vp, C.c_size_t, C.c_int32, vp, P(vp)], C.c_int),
             "pct_batch_count": ([vp, vp], C.c_int),
             "pct_batch_nnz": ([vp, P(C.c_int64), vp], C.c_int),
@@ -320,7 +320,7 @@ class Batch:
     """pct_batch_* over a list of workload dicts: one persistent launch per
     phase for all of them, replayed from CUDA graphs."""
 
-    def __init__(self, workloads, autotune: bool = False, stream=None, device="cuda"):
+    def __init__(self, workloads, autotune: bool = False, stream=None, device="cuda", lean: bool = False):
         import torch
         self.n = len(workloads)
         self.phantoms = [Phantom(w["phantom"]) for w in workloads]
@@ -331,11 +331,12 @@ class Batch:
             BatchItem(p.handle, g.c, rp.data_ptr(), x.data_ptr())
             for p, g, rp, x in zip(self.phantoms, self.geos, self.row_ptr, self.x_true)])
         nbytes = C.c_size_t()
-        _check(lib().pct_batch_workspace_size(self._items, self.n, C.byref(nbytes)))
+        flags = (BATCH_AUTOTUNE if autotune else 0) | (BATCH_LEAN if lean else 0)
+        _check(lib().pct_batch_workspace_size(self._items, self.n, flags, C.byref(nbytes)))
         self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=device)
         self.handle = C.c_void_p()
         _check(lib().pct_batch_create(self._items, self.n, _ptr(self.workspace), nbytes.value,
-                                      BATCH_AUTOTUNE if autotune else 0, _stream(stream),
+                                      flags, _stream(stream),
                                       C.byref(self.handle)))
         self.device = device
 
@@ -373,12 +374,12 @@ class Batch:
             self.handle = None
 
 
-def batch_workspace_size(workloads) -> int:
+def batch_workspace_size(workloads, lean: bool = False) -> int:
     phs = [Phantom(w["phantom"]) for w in workloads]
     geos = [GeometryArgs(w) for w in workloads]
     items = (BatchItem * len(phs))(*[BatchItem(p.handle, g.c, None, None) for p, g in zip(phs, geos)])
     n = C.c_size_t()
-    _check(lib().pct_batch_workspace_size(items, len(phs), C.byref(n)))
+    _check(lib().pct_batch_workspace_size(items, len(phs), BATCH_LEAN if lean else 0, C.byref(n)))
     return n.value
 
 

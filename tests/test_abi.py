@@ -178,3 +178,14 @@ def test_first_row_is_validated(pct):
         with pytest.raises(pct.PctError) as e:
             pct.simulate_workspace_size(ph, pct.GeometryArgs(dict(w, first_row=bad)), pct.PREC_MIXED)
         assert e.value.status == pct.EINVAL and "first_row" in pct.last_error()
+
+
+def test_lean_form_workspace(pct):
+    for w in (W.neo2_2d_spline(n_angles=10, paths_per_angle=1000), W.head_3d_spline(n_angles=4, paths_per_angle=1000)):
+        ph, geo = pct.Phantom(w["phantom"]), pct.GeometryArgs(w)
+        full = pct.simulate_workspace_size(ph, geo, pct.PREC_MIXED)
+        lean = pct.simulate_workspace_size(ph, geo, pct.PREC_MIXED_LEAN)
+        assert lean < 0.25 * full
+        assert lean >= geo.n_rows * (160 + 184 + 2 * 112 + 1)  # row records, lead segments, row flags
+    assert pct.batch_workspace_size(W.batch_instances(count=4, max_paths=50000), lean=True) < \
+        pct.batch_workspace_size(W.batch_instances(count=4, max_paths=50000))
