@@ -280,9 +280,8 @@ typedef struct pct_batch pct_batch; /* opaque */
 pct_status pct_batch_workspace_size(const pct_batch_item* items, int32_t n, int32_t flags, size_t* bytes);
 
 /* Uploads every simulation's tables into the workspace, orders the work
- * items, optionally autotunes the launch shape (runs the count phase a few
- * times and synchronises; the choice is cached per batch signature in the
- * process) and captures the graphs.  The workspace and the item buffers must
+ * items, optionally autotunes the launch shape (runs the count phases a few
+ * times and synchronises; see pct_batch_tuning) and captures the graphs.  The workspace and the item buffers must
  * stay valid until pct_batch_destroy. */
 pct_status pct_batch_create(const pct_batch_item* items, int32_t n, void* workspace_dev, size_t workspace_bytes,
                             int32_t flags, void* stream, pct_batch** out);
@@ -294,13 +293,28 @@ pct_status pct_batch_count(pct_batch* batch, void* stream);
 pct_status pct_batch_nnz(pct_batch* batch, int64_t* nnz, void* stream);
 
 /* fill phase: col_dev[k], val_dev[k], b_dev[k] are item k's outputs (host
- * arrays of n device pointers) */
+ * arrays of n device pointers).  With PCT_BATCH_AUTOTUNE the first call
+ * times the fill's launch shapes on these outputs (synchronises). */
 pct_status pct_batch_fill(pct_batch* batch, int32_t* const* col_dev, float* const* val_dev, float* const* b_dev,
                           void* stream);
 
-/* the launch shape in use: grid multiplier (x resident blocks per SM) and item
- * order (0: item order, 1: largest simulation first) */
-pct_status pct_batch_params(const pct_batch* batch, int32_t* grid_mult, int32_t* order);
+/* The launch shape of a batch.  A phase's work items are blocks of
+ * rows_per_item rows of one simulation; its persistent launch has
+ * grid_mult x (SMs x resident blocks per SM) blocks.  With PCT_BATCH_AUTOTUNE
+ * pct_batch_create times the item order on the count, then rows per item
+ * {64, 128, 256} x grid multiplier {1, 2} for the path set-up and the count
+ * phases; the first pct_batch_fill times the same for the fill phase, with
+ * and without prefetching the next row's segment records into L2 (the
+ * fill's staging depth, 1 row or none), and recaptures the fill graph.
+ * Choices are cached per batch signature in the process. */
+typedef struct {
+  int32_t order;            /* 0: items as given, 1: largest simulation first (2D before 3D either way) */
+  int32_t rows_per_item[3]; /* path set-up, count, fill */
+  int32_t grid_mult[3];     /* path set-up, count, fill */
+  int32_t fill_prefetch;    /* 1: next row's records prefetched into L2 */
+} pct_batch_tuning;
+
+pct_status pct_batch_params(const pct_batch* batch, pct_batch_tuning* out);
 
 pct_status pct_batch_destroy(pct_batch* batch);
 

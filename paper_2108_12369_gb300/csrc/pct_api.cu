@@ -567,13 +567,19 @@ struct pct_batch {
   std::vector<Layout> layouts;
   std::vector<size_t> base;               // workspace offset of each item's region
   std::vector<SimDev> sims;
+  std::vector<BatchInst> by_item;         // order-independent instance fields, by item
   std::vector<BatchInst> inst;            // processing order
   std::vector<int> order;                 // processing position -> item index
+  std::vector<int*> out_col;              // outputs by item (set by pct_batch_fill)
+  std::vector<float*> out_val, out_b;
   BatchInst* d_inst = nullptr;
   unsigned long long* d_next = nullptr;   // two counters (2D, 3D launches)
-  long long first3 = 0, total = 0;
-  int grid_mult = 1, order_mode = 0;
-  bool lean = false;  // PCT_BATCH_LEAN: no segment records, fills rebuild the tables
+  long long first3[3] = {0, 0, 0}, total[3] = {0, 0, 0};  // per phase: first 3D work item, work items
+  pct_batch_tuning tune;                  // the launch shape in use
+  bool lean = false;        // PCT_BATCH_LEAN: no segment records, fills rebuild the tables
+  bool autotune = false;
+  bool fill_tuned = false;  // the fill's shape was timed (or taken from the cache)
+  unsigned long long sig = 0;
   int bps[3][2] = {{1, 1}, {1, 1}, {1, 1}};  // resident blocks per SM [phase][dim 3]
   bool small[2] = {true, true};               // [dim 3]: every instance fits the smaller layout
   int sms = 1;
@@ -583,8 +589,23 @@ struct pct_batch {
 
 namespace {
 
+struct TuneEntry {
+  pct_batch_tuning t;
+  bool fill_tuned;
+};
 std::mutex g_tune_mu;
-std::map<unsigned long long, std::pair<int, int>> g_tune_cache;  // signature -> (grid mult, order)
+std::map<unsigned long long, TuneEntry> g_tune_cache;  // batch signature -> launch shape
+
+pct_batch_tuning default_tuning() {
+  pct_batch_tuning t;
+  t.order = 0;
+  for (int p = 0; p < 3; ++p) {
+    t.rows_per_item[p] = 128;
+    t.grid_mult[p] = 1;
+  }
+  t.fill_prefetch = 1;
+  return t;
+}
 
 unsigned long long batch_signature(const pct_batch& b) {
   unsigned long long h = 1469598103934665603ULL;
@@ -592,6 +613,7 @@ unsigned long long batch_signature(const pct_batch& b) {
     h ^= v;
     h *= 1099511628211ULL;
   };
+  mix(b.lean ? 1ULL : 0ULL);
   for (int k = 0; k < b.n; ++k) {
     const pct_batch_item& it = b.items[k];
     mix((unsigned long long)it.phantom->dev.g.dim);
@@ -602,18 +624,61 @@ unsigned long long batch_signature(const pct_batch& b) {
   return h;
 }
 
+// Processing order (2D instances first, then 3D; within each, item order or
+// largest first) and each phase's work items of rows_per_item[phase] rows;
+// uploads the instance table (with the outputs set so far).
+pct_status batch_arrange(pct_batch& b, cudaStream_t st) {
+  const int n = b.n;
+  std::vector<int> ord(n);
+  for (int k = 0; k < n; ++k) ord[k] = k;
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+    const int dx = b.items[x].phantom->dev.g.dim, dy = b.items[y].phantom->dev.g.dim;
+    if (dx != dy) return dx < dy;
+    if (b.tune.order == 1) return b.layouts[x].rows > b.layouts[y].rows;
+    return false;
+  });
+  b.order = ord;
+  b.inst.resize(n);
+  for (int pos = 0; pos < n; ++pos) {
+    const int k = ord[pos];
+    b.inst[pos] = b.by_item[k];
+    b.inst[pos].col = b.out_col[k];
+    b.inst[pos].val = b.out_val[k];
+    b.inst[pos].b = b.out_b[k];
+  }
+  for (int p = 0; p < 3; ++p) {
+    const long long R = b.tune.rows_per_item[p];
+    long long item = 0;
+    b.first3[p] = -1;
+    for (int pos = 0; pos < n; ++pos) {
+      if (b.first3[p] < 0 && b.inst[pos].S.ph.g.dim == 3) b.first3[p] = item;
+      b.inst[pos].item0[p] = item;
+      item += (b.inst[pos].n + R - 1) / R;
+    }
+    b.total[p] = item;
+    if (b.first3[p] < 0) b.first3[p] = item;
+  }
+  if (cudaMemcpyAsync(b.d_inst, b.inst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return cuda_check("batch table upload");
+  return PCT_OK;
+}
+
+void batch_launch_phase(pct_batch& b, int f, cudaStream_t st) {
+  const pct_batch_tuning& t = b.tune;
+  launch_batch(f, 2, b.small[0], b.lean, b.d_inst, b.n, 0, b.first3[f], b.d_next,
+               b.sms * b.bps[f][0] * t.grid_mult[f], t.rows_per_item[f], t.fill_prefetch, st);
+  launch_batch(f, 3, b.small[1], b.lean, b.d_inst, b.n, b.first3[f], b.total[f], b.d_next + 1,
+               b.sms * b.bps[f][1] * t.grid_mult[f], t.rows_per_item[f], t.fill_prefetch, st);
+}
+
 void batch_phase(pct_batch& b, bool fill, cudaStream_t st) {
   if (!fill) {
     for (int k = 0; k < b.n; ++k)
       launch_raster(b.items[k].phantom->dev, b.items[k].x_true_dev, b.items[k].phantom->nvox, st);
   }
   // count: the FP64 path set-up, then the cooperative count; fill: the fill
-  for (int f = fill ? 2 : 0; f <= (fill ? 2 : 1); ++f) {
-    launch_batch(f, 2, b.small[0], b.lean, b.d_inst, b.n, 0, b.first3, b.d_next, b.sms * b.bps[f][0] * b.grid_mult,
-                 st);
-    launch_batch(f, 3, b.small[1], b.lean, b.d_inst, b.n, b.first3, b.total, b.d_next + 1,
-                 b.sms * b.bps[f][1] * b.grid_mult, st);
-  }
+  for (int f = fill ? 2 : 0; f <= (fill ? 2 : 1); ++f) batch_launch_phase(b, f, st);
   if (!fill) {
     for (int k = 0; k < b.n; ++k)
       launch_scan_rowptr((long long*)b.items[k].row_ptr_dev, b.layouts[k].rows,
@@ -638,13 +703,60 @@ pct_status batch_capture(pct_batch& b, bool fill) {
     return cuda_check("graph capture");
   }
   if (fill) {
+    if (b.e_fill) cudaGraphExecDestroy(b.e_fill);
+    if (b.g_fill) cudaGraphDestroy(b.g_fill);
     b.g_fill = g;
     b.e_fill = e;
   } else {
+    if (b.e_count) cudaGraphExecDestroy(b.e_count);
+    if (b.g_count) cudaGraphDestroy(b.g_count);
     b.g_count = g;
     b.e_count = e;
   }
   return PCT_OK;
+}
+
+// device ms of the given phases (one warm-up run, then one timed run)
+pct_status time_phases(pct_batch& b, int p0, int p1, cudaStream_t st, float* ms) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cuda_check("autotune events");
+  for (int f = p0; f <= p1; ++f) batch_launch_phase(b, f, st);
+  cudaEventRecord(e0, st);
+  for (int f = p0; f <= p1; ++f) batch_launch_phase(b, f, st);
+  cudaEventRecord(e1, st);
+  pct_status rc = PCT_OK;
+  if (cudaEventSynchronize(e1) != cudaSuccess)
+    rc = cuda_check("autotune");
+  else
+    cudaEventElapsedTime(ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+// the best of rows per work item {64, 128, 256} x grid multiplier {1, 2}
+// (x prefetch {0, 1} for the fill) for one phase, the others as they stand
+pct_status tune_phase(pct_batch& b, int f, cudaStream_t st) {
+  const int rows[3] = {64, 128, 256};
+  pct_batch_tuning best = b.tune;
+  float best_ms = 1e30f;
+  for (int pf = (f == 2 ? 0 : 1); pf <= 1; ++pf)
+    for (int ri = 0; ri < 3; ++ri)
+      for (int gm = 1; gm <= 2; ++gm) {
+        b.tune.rows_per_item[f] = rows[ri];
+        b.tune.grid_mult[f] = gm;
+        if (f == 2) b.tune.fill_prefetch = pf;
+        pct_status rc = batch_arrange(b, st);
+        float ms = 0.f;
+        if (rc == PCT_OK) rc = time_phases(b, f, f, st, &ms);
+        if (rc != PCT_OK) return rc;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = b.tune;
+        }
+      }
+  b.tune = best;
+  return batch_arrange(b, st);
 }
 
 }  // namespace
@@ -689,10 +801,15 @@ extern "C" pct_status pct_batch_create(const pct_batch_item* items, int32_t n, v
   if (!b) return fail(PCT_ENOMEM, "out of host memory");
   b->n = n;
   b->lean = form == PCT_PREC_MIXED_LEAN;
+  b->autotune = (flags & PCT_BATCH_AUTOTUNE) != 0;
+  b->tune = default_tuning();
   b->items.assign(items, items + n);
   b->layouts.resize(n);
   b->base.resize(n);
   b->sims.resize(n);
+  b->out_col.assign(n, nullptr);
+  b->out_val.assign(n, nullptr);
+  b->out_b.assign(n, nullptr);
   char* base = (char*)ws;
   size_t off = 0;
   for (int k = 0; k < n; ++k) {
@@ -719,9 +836,9 @@ extern "C" pct_status pct_batch_create(const pct_batch_item* items, int32_t n, v
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
   // instance table contents (order-independent fields)
-  std::vector<BatchInst> by_item(n);
+  b->by_item.resize(n);
   for (int k = 0; k < n; ++k) {
-    BatchInst& I = by_item[k];
+    BatchInst& I = b->by_item[k];
     memset(&I, 0, sizeof(I));
     I.S = b->sims[k];
     I.M = mix_args(b->sims[k], b->layouts[k].rows, (const char*)b->sims[k].cs - b->layouts[k].cs + b->layouts[k].basis32,
@@ -734,91 +851,42 @@ extern "C" pct_status pct_batch_create(const pct_batch_item* items, int32_t n, v
   }
   for (int f = 0; f < 3; ++f)
     for (int d = 0; d < 2; ++d) b->bps[f][d] = batch_blocks_per_sm(f, d == 0 ? 2 : 3, b->small[d], b->lean);
-  auto arrange = [&]() -> pct_status {
-    std::vector<BatchInst> saved = by_item;
-    pct_status r = PCT_OK;
-    // batch_arrange fills item0 in processing order; copy the item fields first
-    b->order.resize(n);
-    for (int k = 0; k < n; ++k) b->order[k] = k;
-    b->inst = saved;
-    std::vector<int> ord(n);
-    for (int k = 0; k < n; ++k) ord[k] = k;
-    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
-      int dx = items[x].phantom->dev.g.dim, dy = items[y].phantom->dev.g.dim;
-      if (dx != dy) return dx < dy;
-      if (b->order_mode == 1) return b->layouts[x].rows > b->layouts[y].rows;
-      return false;
-    });
-    for (int pos = 0; pos < n; ++pos) b->inst[pos] = saved[ord[pos]];
-    b->order = ord;
-    long long item = 0;
-    b->first3 = -1;
-    for (int pos = 0; pos < n; ++pos) {
-      if (b->first3 < 0 && b->inst[pos].S.ph.g.dim == 3) b->first3 = item;
-      b->inst[pos].item0 = item;
-      item += (b->inst[pos].n + 127) / 128;
-    }
-    b->total = item;
-    if (b->first3 < 0) b->first3 = item;
-    if (cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, st) != cudaSuccess)
-      r = cuda_check("batch table upload");
-    if (cudaStreamSynchronize(st) != cudaSuccess) r = cuda_check("batch table upload");
-    return r;
-  };
-  const unsigned long long sig = batch_signature(*b);
+  b->sig = batch_signature(*b);
   bool cached = false;
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    auto itc = g_tune_cache.find(sig);
+    auto itc = g_tune_cache.find(b->sig);
     if (itc != g_tune_cache.end()) {
-      b->grid_mult = itc->second.first;
-      b->order_mode = itc->second.second;
+      b->tune = itc->second.t;
+      b->fill_tuned = itc->second.fill_tuned;
       cached = true;
     }
   }
-  if ((flags & PCT_BATCH_AUTOTUNE) && !cached) {
-    // time the count phase for each launch shape; keep the fastest
-    const int mults[2] = {1, 2};
+  if (b->autotune && !cached) {
+    // item order on the whole count (path + count phases), then each
+    // phase's rows per work item and grid size; the fill's at the first
+    // pct_batch_fill (it needs the outputs)
     float best = 1e30f;
-    int bm = 1, bo = 0;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    for (int om = 0; om < 2; ++om) {
-      for (int mi = 0; mi < 2; ++mi) {
-        b->order_mode = om;
-        b->grid_mult = mults[mi];
-        if ((rc = arrange()) != PCT_OK) break;
-        batch_phase(*b, false, st);  // warm-up
-        cudaEventRecord(e0, st);
-        batch_phase(*b, false, st);
-        cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-          rc = cuda_check("autotune");
-          break;
-        }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-          best = ms;
-          bm = mults[mi];
-          bo = om;
-        }
+    int bo = 0;
+    for (int om = 0; om < 2 && rc == PCT_OK; ++om) {
+      b->tune.order = om;
+      float ms = 0.f;
+      if ((rc = batch_arrange(*b, st)) == PCT_OK && (rc = time_phases(*b, 0, 1, st, &ms)) == PCT_OK && ms < best) {
+        best = ms;
+        bo = om;
       }
-      if (rc != PCT_OK) break;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    b->tune.order = bo;
+    if (rc == PCT_OK) rc = tune_phase(*b, 0, st);
+    if (rc == PCT_OK) rc = tune_phase(*b, 1, st);
     if (rc != PCT_OK) {
       pct_batch_destroy(b);
       return rc;
     }
-    b->grid_mult = bm;
-    b->order_mode = bo;
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune_cache[sig] = std::make_pair(bm, bo);
+    g_tune_cache[b->sig] = TuneEntry{b->tune, false};
   }
-  if ((rc = arrange()) != PCT_OK || (rc = batch_capture(*b, false)) != PCT_OK ||
+  if ((rc = batch_arrange(*b, st)) != PCT_OK || (rc = batch_capture(*b, false)) != PCT_OK ||
       (rc = batch_capture(*b, true)) != PCT_OK) {
     pct_batch_destroy(b);
     return rc;
@@ -851,12 +919,27 @@ extern "C" pct_status pct_batch_fill(pct_batch* b, int32_t* const* col, float* c
                                      void* stream) {
   if (!b || !b->e_fill || !col || !val || !bout) return fail(PCT_EINVAL, "pct_batch_fill: NULL argument");
   cudaStream_t st = (cudaStream_t)stream;
-  for (int pos = 0; pos < b->n; ++pos) {
-    int k = b->order[pos];
+  for (int k = 0; k < b->n; ++k) {
     if (b->layouts[k].rows > 0 && !bout[k]) return fail(PCT_EINVAL, "batch item %d: NULL b", k);
-    b->inst[pos].col = (int*)col[k];
-    b->inst[pos].val = val[k];
-    b->inst[pos].b = bout[k];
+    b->out_col[k] = (int*)col[k];
+    b->out_val[k] = val[k];
+    b->out_b[k] = bout[k];
+  }
+  for (int pos = 0; pos < b->n; ++pos) {
+    const int k = b->order[pos];
+    b->inst[pos].col = b->out_col[k];
+    b->inst[pos].val = b->out_val[k];
+    b->inst[pos].b = b->out_b[k];
+  }
+  if (b->autotune && !b->fill_tuned) {
+    // the fill's shape, timed once on these outputs (a fill rewrites the
+    // same values), then the fill graph recaptured; the choice is cached
+    pct_status rc = tune_phase(*b, 2, st);
+    if (rc == PCT_OK) rc = batch_capture(*b, true);
+    if (rc != PCT_OK) return rc;
+    b->fill_tuned = true;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[b->sig] = TuneEntry{b->tune, true};
   }
   // the graph reads the output pointers from the instance table in global
   // memory, so updating the table is enough (the copy is staged before return)
@@ -866,10 +949,9 @@ extern "C" pct_status pct_batch_fill(pct_batch* b, int32_t* const* col, float* c
   return PCT_OK;
 }
 
-extern "C" pct_status pct_batch_params(const pct_batch* b, int32_t* grid_mult, int32_t* order) {
-  if (!b || !grid_mult || !order) return fail(PCT_EINVAL, "pct_batch_params: NULL argument");
-  *grid_mult = b->grid_mult;
-  *order = b->order_mode;
+extern "C" pct_status pct_batch_params(const pct_batch* b, pct_batch_tuning* out) {
+  if (!b || !out) return fail(PCT_EINVAL, "pct_batch_params: NULL argument");
+  *out = b->tune;
   return PCT_OK;
 }
 

@@ -38,15 +38,20 @@ bool small_cap(int seg_stride, const GridDev& g) {
   return seg_stride <= kSegSmall && planes <= 1536;
 }
 
-// Path phase of one block of 128 consecutive rows starting at row0: thread
-// t forms the FP64 path of row row0 + t (the definition), keeps it and its
-// double-float copy as row records and sets up the row's lead-in and
-// lead-out segments.  The arguments may live in parameter space (one
-// launch per simulation) or in global memory (the batch kernel).
+// rows one block handles at most (the batch's work items take 64 - 256)
+constexpr int kBlockRowsMax = 256;
+
+// Path phase of one block of nr consecutive rows starting at row0 (128
+// threads, thread t takes rows row0 + t, + 128, ...): the FP64 path of each
+// row (the definition), kept with its double-float copy as row records, and
+// the row's lead-in and lead-out segments set up.  The arguments may live in
+// parameter space (one launch per simulation) or in global memory (the
+// batch kernel).
 template <int DIM>
 __device__ __forceinline__ void path_block(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
-                                           long long n, long long row0) {
-  const long long i = row0 + threadIdx.x;
+                                           long long n, long long row0, int nr = 128) {
+  for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+  const long long i = row0 + t;
   if (i < n) {
     PathF64 p = path_setup<DIM>(S, i);
     M.r64[i] = p;  // exact decisions read the FP64 path back from here
@@ -65,6 +70,7 @@ __device__ __forceinline__ void path_block(const SimDev& S, const MixArgs& M, co
       lead[1] = seg_prepare<DIM>(S.ph.g, M.gd, Sg, gdg, Va, Vb, r.mag, ExactRef{Sg, M.r64 + i, r.nv - 2});
     }
   }
+  }
 }
 
 // The block's 128 rows are handed out one at a time to whichever warp is
@@ -77,19 +83,20 @@ __device__ __forceinline__ int next_row_of_block(int* take) {
   return __shfl_sync(0xffffffffu, k, 0);
 }
 
-// Count phase of the same block: each warp counts one row at a time.
+// Count phase of a block of nr rows: each warp counts one row at a time.
 template <int DIM, int CAP>
 __device__ __forceinline__ void rows_block(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
-                                           long long n, long long row0, long long* __restrict__ counts) {
+                                           long long n, long long row0, long long* __restrict__ counts,
+                                           int nr = 128) {
   CoopSmem<DIM, CAP>& sm = warp_smem<CoopSmem<DIM, CAP>>();
   __shared__ int take, n_walk;
-  __shared__ unsigned char walk[128];  // rows the cooperative count declined
+  __shared__ unsigned char walk[kBlockRowsMax];  // rows the cooperative count declined
   if (threadIdx.x == 0) {
     take = 4;
     n_walk = 0;
   }
   __syncthreads();
-  for (int k = threadIdx.x >> 5; k < 128 && row0 + k < n; k = next_row_of_block(&take))
+  for (int k = threadIdx.x >> 5; k < nr && row0 + k < n; k = next_row_of_block(&take))
     if (!coop_count_row<DIM>(S, M, Sg, gdg, row0 + k, sm, counts) && (threadIdx.x & 31) == 0)
       walk[atomicAdd(&n_walk, 1)] = (unsigned char)k;
   // the declined rows after all others: the walker's out-of-line call stays
@@ -114,29 +121,31 @@ __global__ void __launch_bounds__(128, 8) k_count_mixed(SimDev S, MixArgs M, con
   rows_block<DIM, CAP>(S, M, Sg, gdg, n, (long long)blockIdx.x * blockDim.x, counts);
 }
 
-// One block of 128 consecutive rows starting at row0 (fill phase): each
-// warp writes one row at a time.
+// One block of nr consecutive rows starting at row0 (fill phase): each
+// warp writes one row at a time; pf = 1 prefetches the next row's segment
+// records into L2 while a row is written.
 template <int DIM, int CAP, bool LEAN>
 __device__ __forceinline__ void fill_block(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
                                            long long n, long long row0, const long long* __restrict__ row_ptr,
                                            const float* __restrict__ x, int* __restrict__ col,
-                                           float* __restrict__ val, float* __restrict__ b) {
+                                           float* __restrict__ val, float* __restrict__ b, int nr = 128,
+                                           int pf = 1) {
   FillSmem<DIM, CAP, LEAN>& sm = warp_smem<FillSmem<DIM, CAP, LEAN>>();
   const int lane = threadIdx.x & 31;
   const int lines = (M.seg_stride * (int)sizeof(SegG<DIM>) + 127) / 128;
   __shared__ int take, n_walk;
-  __shared__ unsigned char walk[128];  // rows the cooperative fill declined
+  __shared__ unsigned char walk[kBlockRowsMax];  // rows the cooperative fill declined
   if (threadIdx.x == 0) {
     take = 4;
     n_walk = 0;
   }
   __syncthreads();
   int k = threadIdx.x >> 5;
-  while (k < 128 && row0 + k < n) {
+  while (k < nr && row0 + k < n) {
     const long long row = row0 + k;
     const int kn = next_row_of_block(&take);
     // the next row's segment records into L2 while this row is written
-    if (!LEAN && kn < 128 && row0 + kn < n) {
+    if (!LEAN && pf && kn < nr && row0 + kn < n) {
       const long long rn = row0 + kn;
       const char* nx = (const char*)((const SegG<DIM>*)M.segg + rn * (long long)M.seg_stride);
       if (lane < lines) asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + 128 * lane));
@@ -184,11 +193,11 @@ __global__ void __launch_bounds__(128, fill_blocks_per_sm<DIM>()) k_fill_mixed_r
 // rows) of many heterogeneous simulations.  A block takes the next item from
 // a device counter; items are independent, so nothing ever waits.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int batch_find(const BatchInst* __restrict__ B, int n_inst, long long item) {
+__device__ __forceinline__ int batch_find(const BatchInst* __restrict__ B, int n_inst, int phase, long long item) {
   int lo = 0, hi = n_inst - 1;  // last instance whose first item is <= item
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
-    if (B[mid].item0 <= item)
+    if (B[mid].item0[phase] <= item)
       lo = mid;
     else
       hi = mid - 1;
@@ -201,7 +210,7 @@ __device__ __forceinline__ int batch_find(const BatchInst* __restrict__ B, int n
 template <int kPhase, int DIM, int CAP, bool LEAN>
 __global__ void __launch_bounds__(128, kPhase == 0 ? 1 : (kPhase == 1 ? 8 : fill_blocks_per_sm<DIM>()))
     k_batch(const BatchInst* __restrict__ B, int n_inst, long long first, long long last,
-            unsigned long long* next) {
+            unsigned long long* next, int nr, int pf) {
   __shared__ long long item_s;
   for (;;) {
     __syncthreads();
@@ -209,14 +218,14 @@ __global__ void __launch_bounds__(128, kPhase == 0 ? 1 : (kPhase == 1 ? 8 : fill
     __syncthreads();
     const long long item = item_s;
     if (item >= last) return;
-    const BatchInst& I = B[batch_find(B, n_inst, item)];
-    const long long row0 = (item - I.item0) * 128;
+    const BatchInst& I = B[batch_find(B, n_inst, kPhase, item)];
+    const long long row0 = (item - I.item0[kPhase]) * nr;
     if constexpr (kPhase == 2)
-      fill_block<DIM, CAP, LEAN>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, I.row_ptr, I.x, I.col, I.val, I.b);
+      fill_block<DIM, CAP, LEAN>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, I.row_ptr, I.x, I.col, I.val, I.b, nr, pf);
     else if constexpr (kPhase == 1)
-      rows_block<DIM, CAP>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, I.row_ptr_w + 1);
+      rows_block<DIM, CAP>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, I.row_ptr_w + 1, nr);
     else
-      path_block<DIM>(I.S, I.M, &I.S, &I.M.gd, I.n, row0);
+      path_block<DIM>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, nr);
   }
 }
 
@@ -259,37 +268,38 @@ int batch_blocks_per_sm(int phase, int dim, bool small, bool lean) {
 
 template <int kPhase, int DIM, int CAP, bool LEAN>
 static void launch_phase(const BatchInst* B, int n_inst, long long first, long long last, unsigned long long* next,
-                         int grid, cudaStream_t st) {
+                         int grid, int nr, int pf, cudaStream_t st) {
   smem_attr(k_batch<kPhase, DIM, CAP, LEAN>, batch_smem<kPhase, DIM, CAP, LEAN>());
   k_batch<kPhase, DIM, CAP, LEAN><<<grid, 128, batch_smem<kPhase, DIM, CAP, LEAN>(), st>>>(B, n_inst, first, last,
-                                                                                          next);
+                                                                                          next, nr, pf);
 }
 
 template <int kPhase, int DIM>
 static void launch_phase_cap(bool small, bool lean, const BatchInst* B, int n_inst, long long first, long long last,
-                             unsigned long long* next, int grid, cudaStream_t st) {
+                             unsigned long long* next, int grid, int nr, int pf, cudaStream_t st) {
   if (kPhase == 2 && lean) {
     if (small)
-      launch_phase<kPhase, DIM, kSegSmall, true>(B, n_inst, first, last, next, grid, st);
+      launch_phase<kPhase, DIM, kSegSmall, true>(B, n_inst, first, last, next, grid, nr, pf, st);
     else
-      launch_phase<kPhase, DIM, kSegMax, true>(B, n_inst, first, last, next, grid, st);
+      launch_phase<kPhase, DIM, kSegMax, true>(B, n_inst, first, last, next, grid, nr, pf, st);
   } else if (kPhase == 0 || !small) {
-    launch_phase<kPhase, DIM, kSegMax, false>(B, n_inst, first, last, next, grid, st);
+    launch_phase<kPhase, DIM, kSegMax, false>(B, n_inst, first, last, next, grid, nr, pf, st);
   } else {
-    launch_phase<kPhase, DIM, kSegSmall, false>(B, n_inst, first, last, next, grid, st);
+    launch_phase<kPhase, DIM, kSegSmall, false>(B, n_inst, first, last, next, grid, nr, pf, st);
   }
 }
 
 void launch_batch(int phase, int dim, bool small, bool lean, const BatchInst* B, int n_inst, long long first,
-                  long long last, unsigned long long* next, int grid, cudaStream_t st) {
+                  long long last, unsigned long long* next, int grid, int nr, int pf, cudaStream_t st) {
   cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
   if (last <= first || n_inst <= 0) return;
-  if (phase == 0 && dim == 2) launch_phase_cap<0, 2>(small, lean, B, n_inst, first, last, next, grid, st);
-  if (phase == 0 && dim == 3) launch_phase_cap<0, 3>(small, lean, B, n_inst, first, last, next, grid, st);
-  if (phase == 1 && dim == 2) launch_phase_cap<1, 2>(small, lean, B, n_inst, first, last, next, grid, st);
-  if (phase == 1 && dim == 3) launch_phase_cap<1, 3>(small, lean, B, n_inst, first, last, next, grid, st);
-  if (phase == 2 && dim == 2) launch_phase_cap<2, 2>(small, lean, B, n_inst, first, last, next, grid, st);
-  if (phase == 2 && dim == 3) launch_phase_cap<2, 3>(small, lean, B, n_inst, first, last, next, grid, st);
+  nr = nr < 32 ? 32 : (nr > kBlockRowsMax ? kBlockRowsMax : nr);
+  if (phase == 0 && dim == 2) launch_phase_cap<0, 2>(small, lean, B, n_inst, first, last, next, grid, nr, pf, st);
+  if (phase == 0 && dim == 3) launch_phase_cap<0, 3>(small, lean, B, n_inst, first, last, next, grid, nr, pf, st);
+  if (phase == 1 && dim == 2) launch_phase_cap<1, 2>(small, lean, B, n_inst, first, last, next, grid, nr, pf, st);
+  if (phase == 1 && dim == 3) launch_phase_cap<1, 3>(small, lean, B, n_inst, first, last, next, grid, nr, pf, st);
+  if (phase == 2 && dim == 2) launch_phase_cap<2, 2>(small, lean, B, n_inst, first, last, next, grid, nr, pf, st);
+  if (phase == 2 && dim == 3) launch_phase_cap<2, 3>(small, lean, B, n_inst, first, last, next, grid, nr, pf, st);
 }
 
 // ---------------------------------------------------------------------------

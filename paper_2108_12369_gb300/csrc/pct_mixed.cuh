@@ -663,7 +663,7 @@ struct BatchInst {
   SimDev S;
   MixArgs M;
   long long n;
-  long long item0;
+  long long item0[3];       // first work item of each phase (path, count, fill)
   long long* row_ptr_w;     // [n + 1]: counts go to row_ptr_w[1..n]
   const long long* row_ptr; // the same array, read by the fill
   const float* x;
@@ -680,7 +680,8 @@ MixArgs mix_args(const SimDev& S, long long n, const void* tab, void* rec, bool 
 bool small_cap(int seg_stride, const GridDev& g);
 // small: every instance of that dimension fits the smaller layout
 int batch_blocks_per_sm(int phase, int dim, bool small, bool lean = false);
+// nr: rows per work item (32..256), pf: fill prefetch of the next row's records
 void launch_batch(int phase, int dim, bool small, bool lean, const BatchInst* B, int n_inst, long long first,
-                  long long last, unsigned long long* next, int grid, cudaStream_t st);
+                  long long last, unsigned long long* next, int grid, int nr, int pf, cudaStream_t st);
 
 }  // namespace pct

@@ -56,6 +56,11 @@ class Csr(C.Structure):
                 ("b", C.c_void_p), ("x_true", C.c_void_p)]
 
 
+class BatchTuning(C.Structure):
+    _fields_ = [("order", C.c_int32), ("rows_per_item", C.c_int32 * 3), ("grid_mult", C.c_int32 * 3),
+                ("fill_prefetch", C.c_int32)]
+
+
 class BatchItem(C.Structure):
     _fields_ = [("phantom", C.c_void_p), ("geo", Geometry), ("row_ptr_dev", C.c_void_p),
                 ("x_true_dev", C.c_void_p)]
@@ -110,7 +115,7 @@ def lib():
             "pct_batch_count": ([vp, vp], C.c_int),
             "pct_batch_nnz": ([vp, P(C.c_int64), vp], C.c_int),
             "pct_batch_fill": ([vp, P(vp), P(vp), P(vp), vp], C.c_int),
-            "pct_batch_params": ([vp, P(C.c_int32), P(C.c_int32)], C.c_int),
+            "pct_batch_params": ([vp, P(BatchTuning)], C.c_int),
             "pct_batch_destroy": ([vp], C.c_int),
             "pct_sap_workspace_size": ([C.c_int64, C.c_int32, P(C.c_size_t)], C.c_int),
             "pct_sap": ([P(Csr), vp, C.c_int32, P(C.c_double), C.c_double, C.c_int32, vp, vp, C.c_size_t, vp],
@@ -364,9 +369,11 @@ class Batch:
                                                   nnz, self.geos)]
 
     def params(self):
-        gm, order = C.c_int32(), C.c_int32()
-        _check(lib().pct_batch_params(self.handle, C.byref(gm), C.byref(order)))
-        return gm.value, order.value
+        """The launch shape in use (pct_batch_tuning) as a dict."""
+        t = BatchTuning()
+        _check(lib().pct_batch_params(self.handle, C.byref(t)))
+        return {"order": t.order, "rows_per_item": list(t.rows_per_item), "grid_mult": list(t.grid_mult),
+                "fill_prefetch": t.fill_prefetch}
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:

@@ -31,11 +31,15 @@ def test_batch_equals_standalone_runs(pct, autotune):
     ws = _instances()
     assert {w["phantom"]["dim"] for w in ws} == {2, 3}
     batch = pct.Batch(ws, autotune=autotune)
-    gm, order = batch.params()
-    assert gm in (1, 2) and order in (0, 1)
-    for rep in range(2):  # graph replay
+    t = batch.params()
+    assert t["order"] in (0, 1) and t["fill_prefetch"] in (0, 1)
+    assert all(r in (64, 128, 256) for r in t["rows_per_item"]) and all(g in (1, 2) for g in t["grid_mult"])
+    for rep in range(2):  # graph replay (the first fill tunes the fill's shape when asked)
         batch.count()
         outs = batch.fill()
+        if autotune and rep == 0:
+            t1 = batch.params()
+            assert t1["rows_per_item"][:2] == t["rows_per_item"][:2] and t1["order"] == t["order"]
         torch.cuda.synchronize()
         for w, o in zip(ws, outs):
             ref = pct.simulate(pct.Phantom(w["phantom"]), pct.GeometryArgs(w), pct.PREC_MIXED)
