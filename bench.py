@@ -597,6 +597,44 @@ def run_batch(args):
           flush=True)
 
 
+def run_sap(args):
+    """Reconstruction (Sec. II-D, III): SAP with the paper's settings -- M =
+    100 strings, lambda = 0.1, 20 iterations from x = 0 -- on simulated NEO 1
+    (constant 1 mm chords, as the paper's examples) and NEO 2 (exact chords,
+    spline paths) systems.  Reports the time per iteration and the relative
+    image error and residual."""
+    import torch
+
+    from paper_2108_12369_gb300 import build as B, pct
+    torch.cuda.set_device(0)
+    B.build()
+    out = {"metric": "SAP iterations/s", "unit": "iterations/s", "n_gpus": 1, "higher_is_better": True,
+           "data": "synthetic", "cases": {}}
+    cases = {"neo1_2d_straight_constant_chord": W.neo1_2d_straight(n_angles=180, paths_per_angle=1000),
+             "neo2_2d_spline": W.neo2_2d_spline(n_angles=360, paths_per_angle=2000, n=200, h=1.0)}
+    cases["neo1_2d_straight_constant_chord"]["model"] = dict(
+        cases["neo1_2d_straight_constant_chord"]["model"], chord=W.CHORD_CONSTANT)
+    for name, w in cases.items():
+        ph, geo = pct.Phantom(w["phantom"]), pct.GeometryArgs(w)
+        sim = pct.simulate(ph, geo, pct.PREC_MIXED)
+        n = ph.nvox
+        ws = torch.empty(pct.sap_workspace_size(n, 100), dtype=torch.uint8, device="cuda")
+        x = torch.zeros(n, dtype=torch.float32, device="cuda")
+        pct.sap(sim, sim["b"], n, 100, 0.1, 1, x, workspace=ws)  # warm-up
+        x.zero_()
+        ms = _timed(lambda: pct.sap(sim, sim["b"], n, 100, 0.1, 20, x, workspace=ws), 1)
+        A = torch.sparse_csr_tensor(sim["row_ptr"], sim["col"].long(), sim["val"], size=(geo.n_rows, n))
+        xt = sim["x_true"]
+        out["cases"][name] = {"rows": geo.n_rows, "nnz": sim["nnz"], "strings": 100, "lambda": 0.1, "iterations": 20,
+                              "ms_per_iteration": ms / 20,
+                              "rel_image_error": (torch.linalg.norm(x - xt) / torch.linalg.norm(xt)).item(),
+                              "rel_residual": (torch.linalg.norm(A @ x - sim["b"]) /
+                                               torch.linalg.norm(sim["b"])).item()}
+        del sim, ws, A
+    out["value"] = 1e3 / out["cases"]["neo2_2d_spline"]["ms_per_iteration"]
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -614,8 +652,9 @@ def main():
     ap.add_argument("--angles", type=int, default=0, help="override the angle count (profiling)")
     ap.add_argument("--paths-per-angle", type=int, default=0, help="override protons per angle (profiling)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host round trip (CSR larger than host RAM)")
-    ap.add_argument("--mode", choices=["csr", "project", "batch"], default="csr",
-                    help="csr: the headline CSR generation; project / batch: the projector and batch rows")
+    ap.add_argument("--mode", choices=["csr", "project", "batch", "sap"], default="csr",
+                    help="csr: the headline CSR generation; project / batch / sap: the projector, batch and "
+                         "reconstruction rows")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-max-paths", type=int, default=2_000_000)
     ap.add_argument("--batch-form", choices=["auto", "mixed", "lean"], default="auto")
@@ -626,6 +665,8 @@ def main():
         run_project(args)
     elif args.mode == "batch":
         run_batch(args)
+    elif args.mode == "sap":
+        run_sap(args)
     else:
         run_ours(args)
 
