@@ -52,8 +52,8 @@ KERNEL_FILES = {
     "f64": ["pct_f64.cu", "pct_device.cuh"],
 }
 FILL_KERNEL = {"mixed": "k_fill_mixed", "f64": "k_fill_f64"}
-# our kernels launched per step: raster, path set-up + count (mixed) or count (f64), 3 scan passes, fill
-LAUNCHES_PER_STEP = {"mixed": 7, "f64": 6}
+# our kernels launched per step: raster, path set-up + lead segments + count (mixed) or count (f64), 3 scan passes, fill
+LAUNCHES_PER_STEP = {"mixed": 8, "f64": 6}
 
 
 def workload(name: str, angles: int = 0, paths_per_angle: int = 0):

@@ -43,10 +43,12 @@ constexpr int kBlockRowsMax = 256;
 
 // Path phase of one block of nr consecutive rows starting at row0 (128
 // threads, thread t takes rows row0 + t, + 128, ...): the FP64 path of each
-// row (the definition), kept with its double-float copy as row records, and
-// the row's lead-in and lead-out segments set up.  The arguments may live in
-// parameter space (one launch per simulation) or in global memory (the
-// batch kernel).
+// row (the definition), kept with its double-float copy as row records.  The
+// kernel is bound by the FP64 pipe; the rows' lead segments are set up by a
+// kernel of their own (lead_block), whose FP32 work would otherwise raise
+// this kernel's registers (126 -> 204) and halve its occupancy.  The
+// arguments may live in parameter space (one launch per simulation) or in
+// global memory (the batch kernel).
 template <int DIM>
 __device__ __forceinline__ void path_block(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
                                            long long n, long long row0, int nr = 128) {
@@ -59,6 +61,20 @@ __device__ __forceinline__ void path_block(const SimDev& S, const MixArgs& M, co
     RowDF r;
     make_rowdf<DIM>(p, S.R, fac, r);
     M.rdf[i] = r;
+  }
+  }
+}
+
+// The lead-in and lead-out segments (vertices 0 -> 1 and nv-2 -> nv-1) of
+// rows [row0, row0 + nr) set up, thread per row, after the path phase (the
+// count's table reads them).
+template <int DIM>
+__device__ __forceinline__ void lead_block(const SimDev& S, const MixArgs& M, const SimDev* Sg, const GridDF* gdg,
+                                           long long n, long long row0, int nr) {
+  for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+    const long long i = row0 + t;
+    if (i >= n) break;
+    const RowDF& r = M.rdf[i];
     SegP<DIM>* lead = lead_rec<DIM>(M, i);
     df Va[3], Vb[3];
     vertex_df<DIM>(r, M.tab, M.R, 0, Va);
@@ -69,7 +85,6 @@ __device__ __forceinline__ void path_block(const SimDev& S, const MixArgs& M, co
       vertex_df<DIM>(r, M.tab, M.R, r.nv - 1, Vb);
       lead[1] = seg_prepare<DIM>(S.ph.g, M.gd, Sg, gdg, Va, Vb, r.mag, ExactRef{Sg, M.r64 + i, r.nv - 2});
     }
-  }
   }
 }
 
@@ -113,6 +128,12 @@ template <int DIM>
 __global__ void __launch_bounds__(128) k_path_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
                                                     long long n) {
   path_block<DIM>(S, M, Sg, gdg, n, (long long)blockIdx.x * blockDim.x);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(128) k_lead_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
+                                                    long long n) {
+  lead_block<DIM>(S, M, Sg, gdg, n, (long long)blockIdx.x * blockDim.x, blockDim.x);
 }
 
 template <int DIM, int CAP>
@@ -224,8 +245,10 @@ __global__ void __launch_bounds__(128, kPhase == 0 ? 1 : (kPhase == 1 ? 8 : fill
       fill_block<DIM, CAP, LEAN>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, I.row_ptr, I.x, I.col, I.val, I.b, nr, pf);
     else if constexpr (kPhase == 1)
       rows_block<DIM, CAP>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, I.row_ptr_w + 1, nr);
-    else
+    else {
       path_block<DIM>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, nr);
+      lead_block<DIM>(I.S, I.M, &I.S, &I.M.gd, I.n, row0, nr);  // (each thread reads its own rows' records)
+    }
   }
 }
 
@@ -482,9 +505,11 @@ void launch_count_mixed(const SimDev& S, const void* tab, long long n, void* rec
   const bool small = small_cap(M.seg_stride, S.ph.g);
   if (S.ph.g.dim == 2) {
     k_path_mixed<2><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n);
+    k_lead_mixed<2><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n);
     launch_count_cap<2>(small, blocks, S, M, Sg, gdg, n, counts, st);
   } else {
     k_path_mixed<3><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n);
+    k_lead_mixed<3><<<blocks, threads, 0, st>>>(S, M, Sg, gdg, n);
     launch_count_cap<3>(small, blocks, S, M, Sg, gdg, n, counts, st);
   }
 }
