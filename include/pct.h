@@ -212,8 +212,8 @@ pct_status pct_simulate_fill(const pct_phantom* ph, const pct_geometry* geo, int
  * pct_simulate_fill writes to device memory.  The rows are filled block by
  * block into staging_dev (caller-owned device memory, 256-byte aligned, two
  * halves; each half holds up to E = (staging_bytes / 2) / 8.25 entries and
- * E / 16 rows), and each block's copy to the host runs on an internal
- * stream while the next block is filled.  Host buffers should be pinned
+ * E / 16 rows), and each block's copies to the host run on two internal
+ * streams (col; val and b) while the next block is filled.  Host buffers should be pinned
  * (page-locked) for the copies to overlap.  Synchronises: on return the
  * host buffers are complete.  EINVAL if a single row has more entries than
  * a half holds.  Caller owns every buffer. */

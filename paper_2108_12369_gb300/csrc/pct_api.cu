@@ -368,24 +368,31 @@ extern "C" pct_status pct_simulate_fill_host(const pct_phantom* ph, const pct_ge
   const long long* rph = (const long long*)row_ptr_host;
   if (rph[L.rows] > 0 && (!col_host || !val_host))
     return fail(PCT_EINVAL, "pct_simulate_fill_host: NULL col_host or val_host for %lld nonzeros", rph[L.rows]);
-  cudaStream_t cs = nullptr;
-  cudaEvent_t ev_fill[2] = {nullptr, nullptr}, ev_copy[2] = {nullptr, nullptr};
+  // two copy streams (col on one, val and b on the other: two copy engines
+  // move the block at once); a half is refilled only after both its copies
+  cudaStream_t cs[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fill[2] = {nullptr, nullptr}, ev_copy[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   auto cleanup = [&]() {
-    if (cs) cudaStreamSynchronize(cs);
+    for (int c = 0; c < 2; ++c)
+      if (cs[c]) cudaStreamSynchronize(cs[c]);
     cudaStreamSynchronize(st);
     for (int h = 0; h < 2; ++h) {
       if (ev_fill[h]) cudaEventDestroy(ev_fill[h]);
-      if (ev_copy[h]) cudaEventDestroy(ev_copy[h]);
+      for (int c = 0; c < 2; ++c)
+        if (ev_copy[h][c]) cudaEventDestroy(ev_copy[h][c]);
     }
-    if (cs) cudaStreamDestroy(cs);
+    for (int c = 0; c < 2; ++c)
+      if (cs[c]) cudaStreamDestroy(cs[c]);
   };
-  bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+  bool ok = cudaStreamCreateWithFlags(&cs[0], cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&cs[1], cudaStreamNonBlocking) == cudaSuccess;
   for (int h = 0; ok && h < 2; ++h)
     ok = cudaEventCreateWithFlags(&ev_fill[h], cudaEventDisableTiming) == cudaSuccess &&
-         cudaEventCreateWithFlags(&ev_copy[h], cudaEventDisableTiming) == cudaSuccess;
+         cudaEventCreateWithFlags(&ev_copy[h][0], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ev_copy[h][1], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cleanup();
-    return cuda_check("pct_simulate_fill_host: stream / events");
+    return cuda_check("pct_simulate_fill_host: streams / events");
   }
   char* base = (char*)staging;
   long long r0 = 0;
@@ -404,8 +411,10 @@ extern "C" pct_status pct_simulate_fill_host(const pct_phantom* ph, const pct_ge
     int* col_s = (int*)(base + h * half);
     float* val_s = (float*)(base + h * half + 4 * E);
     float* b_s = (float*)(base + h * half + 8 * E);
-    if (k >= 2) ok = cudaStreamWaitEvent(st, ev_copy[h], 0) == cudaSuccess;
-    if (!ok) break;  // never refill a half whose copy may still be running
+    if (k >= 2)
+      ok = cudaStreamWaitEvent(st, ev_copy[h][0], 0) == cudaSuccess &&
+           cudaStreamWaitEvent(st, ev_copy[h][1], 0) == cudaSuccess;
+    if (!ok) break;  // never refill a half whose copies may still be running
     if (precision == PCT_PREC_F64)  // col / val by CSR position: bases moved back by nz0 (host arithmetic)
       launch_fill_f64(S, r0, r1 - r0, (const long long*)row_ptr_dev + r0, x,
                       (int*)((uintptr_t)col_s - sizeof(int) * (uintptr_t)nz0),
@@ -415,18 +424,20 @@ extern "C" pct_status pct_simulate_fill_host(const pct_phantom* ph, const pct_ge
                         (const long long*)row_ptr_dev, x, col_s, val_s, b_s, (char*)ws + L.args, st, r0, r1, nz0,
                         k == 0, precision == PCT_PREC_MIXED_LEAN);
     ok = ok && cudaGetLastError() == cudaSuccess && cudaEventRecord(ev_fill[h], st) == cudaSuccess &&
-         cudaStreamWaitEvent(cs, ev_fill[h], 0) == cudaSuccess;
+         cudaStreamWaitEvent(cs[0], ev_fill[h], 0) == cudaSuccess &&
+         cudaStreamWaitEvent(cs[1], ev_fill[h], 0) == cudaSuccess;
     if (ok && nz1 > nz0)
-      ok = cudaMemcpyAsync(col_host + nz0, col_s, 4 * (size_t)(nz1 - nz0), cudaMemcpyDeviceToHost, cs) ==
+      ok = cudaMemcpyAsync(col_host + nz0, col_s, 4 * (size_t)(nz1 - nz0), cudaMemcpyDeviceToHost, cs[0]) ==
                cudaSuccess &&
-           cudaMemcpyAsync(val_host + nz0, val_s, 4 * (size_t)(nz1 - nz0), cudaMemcpyDeviceToHost, cs) ==
+           cudaMemcpyAsync(val_host + nz0, val_s, 4 * (size_t)(nz1 - nz0), cudaMemcpyDeviceToHost, cs[1]) ==
                cudaSuccess;
     ok = ok &&
-         cudaMemcpyAsync(b_host + r0, b_s, 4 * (size_t)(r1 - r0), cudaMemcpyDeviceToHost, cs) == cudaSuccess &&
-         cudaEventRecord(ev_copy[h], cs) == cudaSuccess;
+         cudaMemcpyAsync(b_host + r0, b_s, 4 * (size_t)(r1 - r0), cudaMemcpyDeviceToHost, cs[1]) == cudaSuccess &&
+         cudaEventRecord(ev_copy[h][0], cs[0]) == cudaSuccess && cudaEventRecord(ev_copy[h][1], cs[1]) == cudaSuccess;
     r0 = r1;
   }
-  ok = ok && cudaStreamSynchronize(cs) == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
+  ok = ok && cudaStreamSynchronize(cs[0]) == cudaSuccess && cudaStreamSynchronize(cs[1]) == cudaSuccess &&
+       cudaStreamSynchronize(st) == cudaSuccess;
   if (!ok) {
     const pct_status e = cuda_check("pct_simulate_fill_host");
     cleanup();
