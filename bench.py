@@ -381,7 +381,7 @@ def run_ours(args):
     h_val = torch.empty(1 if small else max(nnz, 1), dtype=torch.float32, pin_memory=True)
     h_b = torch.empty(1 if small else max(n_rows, 1), dtype=torch.float32, pin_memory=True)
     staging = torch.empty(256 if small else 1 << 30, dtype=torch.uint8, device=dev)
-    e2e_steps = 0 if small else max(1, min(args.steps, 3))
+    e2e_steps = 0 if small else max(1, min(args.steps, 5))
 
     def step_host():
         pct.phantom_rasterize(ph, x)
@@ -392,16 +392,17 @@ def run_ours(args):
 
     for _ in range(args.warmup if e2e_steps else 0):
         step_host()  # warm-up (first launches, first writes to the pinned pages), untimed
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ee = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps + 1)]
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    e0.record(stream)
-    for _ in range(e2e_steps):
+    ee[0].record(stream)
+    for k in range(e2e_steps):
         step_host()
-    e1.record(stream)
+        ee[k + 1].record(stream)
     torch.cuda.synchronize()
-    e2e_s = e0.elapsed_time(e1) / 1e3
+    e2e_step_ms = [ee[k].elapsed_time(ee[k + 1]) for k in range(e2e_steps)]
+    e2e_s = sum(e2e_step_ms) / 1e3
     if world > 1:
         t = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -447,7 +448,7 @@ def run_ours(args):
         "wall_s_timed_loop": t_wall,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": e2e_steps},
+                "steps": e2e_steps, "step_ms": [round(v, 2) for v in e2e_step_ms]},
         "gpu_launches": LAUNCHES_PER_STEP[args.precision] * args.steps,
     }
     if other is not None:
