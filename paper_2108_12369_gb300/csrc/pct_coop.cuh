@@ -456,67 +456,12 @@ struct Axes {
   int n[DIM], dc[DIM], ax[DIM];   // crossings, column step, original axis
 };
 
-template <int DIM>
-__device__ __forceinline__ Axes<DIM> rotate(const SegR<DIM>& R, int a, const int (&stride)[3]) {
-  using W = SegW<DIM>;
-  float p0[DIM], h[DIM], c[DIM];
-  int n[DIM], dc[DIM];
-  const int misc = R.w[W::MISC];
-#pragma unroll
-  for (int k = 0; k < DIM; ++k) {
-    p0[k] = R.f(W::PH0 + k);
-    h[k] = R.f(W::HV + k);
-    c[k] = R.f(W::CB + k);
-    n[k] = R.cnt(k);
-    dc[k] = ((misc >> (4 + k)) & 1) ? -stride[k] : stride[k];
-  }
-  Axes<DIM> X;
-  // slot 0: axis a; slots 1..: the others in increasing order
-  int order[DIM];
-  if constexpr (DIM == 2) {
-    order[0] = a;
-    order[1] = 1 - a;
-  } else {
-    order[0] = a;
-    order[1] = a == 0 ? 1 : 0;
-    order[2] = a == 2 ? 1 : 2;
-  }
-#pragma unroll
-  for (int k = 0; k < DIM; ++k) {
-    const int o = order[k];
-    X.p0[k] = pick<DIM>(p0, o);
-    X.h[k] = pick<DIM>(h, o);
-    X.c[k] = pick<DIM>(c, o);
-    X.n[k] = pick<DIM>(n, o);
-    X.dc[k] = pick<DIM>(dc, o);
-    X.ax[k] = o;
-  }
-  return X;
-}
-
 struct Cross {
   int rank;   // position among the segment's crossings
   int colv;   // voxel entered
   float nv;   // offset of the next crossing (the segment's end after the last)
   bool last;
 };
-
-// exact tie of crossing i of axis A with a plane of an axis below it:
-// common path from the FP32 bounds, *unsure where they cannot decide
-template <int DIM, int A>
-__device__ __forceinline__ void tie_axis(const SegR<DIM>& R, int i, bool& unsure) {
-  using W = SegW<DIM>;
-  const float p0a = R.f(W::PH0 + A), ha = R.f(W::HV + A), ca = R.f(W::CB + A);
-  const float ph = fmaf((float)i, ha, p0a);
-#pragma unroll
-  for (int c = 0; c < A; ++c) {
-    const float p0c = R.f(W::PH0 + c), hc = R.f(W::HV + c), cc = R.f(W::CB + c);
-    const float jf = rintf(__fdividef(ph - p0c, hc));
-    const float pb = fmaf(jf, hc, p0c);
-    const int j = (int)jf;
-    unsure = unsure || (j >= 0 && j < R.cnt(c) && !(fabsf(ph - pb) > fmaf(8.f * kU32, ph + fabsf(pb), ca + cc)));
-  }
-}
 
 // Crossing i of axis A (known at compile time) from the fill's arrays:
 // ax[c] = (ph0, hv, 1/hv, cb), cn = (crossings per axis, start column),
@@ -620,36 +565,35 @@ static __device__ __noinline__ Cross cross_exact(const SimDev* Sg, const PathF64
   return o;
 }
 
+// field a of a record's per-axis group k0 (selects, no indexing)
 template <int DIM>
-static __device__ __noinline__ bool tie_exact(const SimDev* Sg, const PathF64* p64, int s, Axes<DIM> X, int i,
-                                              int col0, int misc) {
-  const GridDev& g = Sg->ph.g;
-  const ExactRef ref{Sg, p64, s};
-  const float ph = fmaf((float)i, X.h[0], X.p0[0]);
-  bool tie = false;
-  for (int k = 1; k < DIM; ++k) {
-    if (X.ax[k] > X.ax[0]) continue;
-    const float jf = rintf(__fdividef(ph - X.p0[k], X.h[k]));
-    const float pb = fmaf(jf, X.h[k], X.p0[k]);
-    const int j = (int)jf;
-    if (j >= 0 && j < X.n[k] && !(fabsf(ph - pb) > fmaf(8.f * kU32, ph + fabsf(pb), X.c[0] + X.c[k])))
-      tie = tie || exact_cmp(ref, X.ax[0], plane_of<DIM>(g, col0, misc, X.ax[0], i), X.ax[k],
-                             plane_of<DIM>(g, col0, misc, X.ax[k], (int)jf)) == 0;
-  }
-  return tie;
+__device__ __forceinline__ float rec_f(const SegR<DIM>& R, int k0, int a) {
+  return a == 0 ? R.f(k0) : (a == 1 || DIM == 2 ? R.f(k0 + 1) : R.f(k0 + DIM - 1));
 }
 
-// Crossings of axis A of the row's segments, 32 per round: marks each
-// segment's first one and returns their number (positions are counted
-// segment after segment; sm.aux[s] = segment s's first position).
-template <int A, class SM>
-__device__ __forceinline__ int axis_starts(SM& sm, int nseg, int lane) {
-  int n[2] = {0, 0}, base[2], t0, t1;
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int s = lane + 32 * h;
-    if (s < nseg) n[h] = sm.cnt(s, A);
-  }
+// exact tie of crossing i of axis u with the nearest plane of axis v
+template <int DIM>
+static __device__ __noinline__ bool tie_exact(const SimDev* Sg, const PathF64* p64, int s, const SegG<DIM>* rec, int u,
+                                              int v, int i) {
+  using W = SegW<DIM>;
+  const SegR<DIM> R = load_seg<DIM>(*rec);
+  const float ph = fmaf((float)i, rec_f<DIM>(R, W::HV, u), rec_f<DIM>(R, W::PH0, u));
+  const float jf = rintf(__fdividef(ph - rec_f<DIM>(R, W::PH0, v), rec_f<DIM>(R, W::HV, v)));
+  const int j = (int)jf;
+  if (j < 0 || j >= R.cnt(v)) return false;
+  const GridDev& g = Sg->ph.g;
+  const int col0 = R.w[W::COL0], misc = R.w[W::MISC];
+  return exact_cmp(ExactRef{Sg, p64, s}, u, plane_of<DIM>(g, col0, misc, u, i), v, plane_of<DIM>(g, col0, misc, v, j)) ==
+         0;
+}
+
+// Items of a pass over the row's segments, 32 per round (segment s on lane
+// s % 32 holds n[s / 32] of them): marks each segment's first one and
+// returns their number (positions are counted segment after segment;
+// sm.aux[s] = segment s's first position).
+template <class SM>
+__device__ __forceinline__ int pass_starts(SM& sm, int nseg, int lane, const int (&n)[2]) {
+  int base[2], t0, t1;
   base[0] = warp_excl_scan(n[0], lane, &t0);
   base[1] = warp_excl_scan(n[1], lane, &t1) + t0;
   __syncwarp();  // the previous pass has finished reading aux, bits and ord
@@ -660,11 +604,43 @@ __device__ __forceinline__ int axis_starts(SM& sm, int nseg, int lane) {
   return t0 + t1;
 }
 
-template <int DIM, int A, class SM>
-__device__ __forceinline__ void tie_rows(SM& sm, int nseg, int lane, const SimDev* Sg, const PathF64* p64,
-                                         const int (&stride)[3], bool& tie, bool& overflow) {
+// the crossings of axis A
+template <int A, class SM>
+__device__ __forceinline__ int axis_starts(SM& sm, int nseg, int lane) {
+  int n[2] = {0, 0};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int s = lane + 32 * h;
+    if (s < nseg) n[h] = sm.cnt(s, A);
+  }
+  return pass_starts(sm, nseg, lane, n);
+}
+
+// Exact ties between crossings of different axes, every pair of axes in one
+// pass.  A tie is a crossing of each axis of the pair at the same point, so
+// it is found from either side: for each pair the pass takes the crossings
+// of the axis with fewer of them in the segment, each against the nearest
+// plane of the other axis.  FP32 bounds settle almost all; the crossings
+// they cannot settle are queued and decided by the FP64 definition after
+// the pass (no call in the loop); *overflow when the queue was full.
+template <int DIM, class SM>
+__device__ __forceinline__ void tie_pass(SM& sm, int nseg, int lane, const SimDev* Sg, const PathF64* p64, bool& tie,
+                                         bool& overflow) {
   using W = SegW<DIM>;
-  const int tot = axis_starts<A>(sm, nseg, lane);
+  int n[2] = {0, 0};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int s = lane + 32 * h;
+    if (s < nseg) {
+      const int n0 = sm.cnt(s, 0), n1 = sm.cnt(s, 1);
+      n[h] = min(n0, n1);
+      if constexpr (DIM > 2) {
+        const int n2 = sm.cnt(s, 2);
+        n[h] += min(n0, n2) + min(n1, n2);
+      }
+    }
+  }
+  const int tot = pass_starts(sm, nseg, lane, n);
   if (lane == 0) sm.qn = 0;
   __syncwarp();
   int ordbase = 0;
@@ -672,26 +648,49 @@ __device__ __forceinline__ void tie_rows(SM& sm, int nseg, int lane, const SimDe
     const int s = seg_at(sm.bits, sm.ord, p0, lane, ordbase);
     const int p = p0 + lane;
     if (p < tot) {
-      const SegR<DIM> R = load_seg<DIM>(sm.tab[s]);
-      const int i = p - sm.aux[s];
-      bool unsure = false;
-      tie_axis<DIM, A>(R, i, unsure);
-      if (unsure) {
+      const int* wi = reinterpret_cast<const int*>(&sm.tab[s]);
+      const float* wf = reinterpret_cast<const float*>(wi);
+      const int c01 = wi[W::CNT];
+      const int n0 = c01 & 0xffff, n1 = (int)((unsigned)c01 >> 16);
+      int i = p - sm.aux[s];
+      // the pair (c, a) of item i: (0, 1), then (0, 2) and (1, 2)
+      int a = 1, c = 0, na = n1, nc = n0;
+      if constexpr (DIM > 2) {
+        const int n2 = wi[W::CNT + 1] & 0xffff;
+        const int m01 = min(n0, n1);
+        if (i >= m01) {
+          i -= m01;
+          a = 2;
+          na = n2;
+          const int m02 = min(n0, n2);
+          if (i >= m02) {
+            i -= m02;
+            c = 1;
+            nc = n1;
+          }
+        }
+      }
+      const bool first_a = na <= nc;
+      const int u = first_a ? a : c, v = first_a ? c : a, nv = first_a ? nc : na;
+      const float ph = fmaf((float)i, wf[W::HV + u], wf[W::PH0 + u]);
+      const float p0v = wf[W::PH0 + v], hv = wf[W::HV + v];
+      const float jf = rintf(__fdividef(ph - p0v, hv));
+      const float pb = fmaf(jf, hv, p0v);
+      const int j = (int)jf;
+      if (j >= 0 && j < nv && !(fabsf(ph - pb) > fmaf(8.f * kU32, ph + fabsf(pb), wf[W::CB + u] + wf[W::CB + v]))) {
         const int k = atomicAdd(&sm.qn, 1);
         if (k < SM::kQ)
-          sm.q[k] = s | (i << 8);
+          sm.q[k] = s | (u << 8) | (v << 10) | (i << 12);
         else
           overflow = true;
       }
     }
   }
   __syncwarp();
-  // the crossings the FP32 bounds could not settle
   const int nq = min(sm.qn, SM::kQ);
   for (int k = lane; k < nq; k += 32) {
-    const int s = sm.q[k] & 0xff, i = sm.q[k] >> 8;
-    const SegR<DIM> R = load_seg<DIM>(sm.tab[s]);
-    tie = tie || tie_exact<DIM>(Sg, p64, s, rotate<DIM>(R, A, stride), i, R.w[W::COL0], R.w[W::MISC]);
+    const int e = sm.q[k], s = e & 0xff;
+    tie = tie || tie_exact<DIM>(Sg, p64, s, &sm.tab[s], (e >> 8) & 3, (e >> 10) & 3, e >> 12);
   }
   __syncwarp();
 }
@@ -934,19 +933,16 @@ __device__ __forceinline__ bool coop_count_row(const SimDev& S, const MixArgs& M
   const GridDev& g = S.ph.g;
   const RowDF& r = M.rdf[row];
   const int nseg = r.nv - 1;
-  const int stride[3] = {1, g.n[0], g.n[0] * (DIM > 2 ? g.n[1] : 1)};
   const PathF64* p64 = M.r64 + row;
   bool irregular = nseg > SM::kCap || nseg < 1 || nseg > M.seg_stride;
   if (!irregular) {
     int totE = 0;
     irregular = !row_table<DIM, SM::kCross>(S, M, Sg, gdg, row, nseg, sm.tab, &totE);
 
-    // 3. exact ties between crossings of different axes (each crossing of
-    // axis a >= 1 against the nearest planes of the axes below it)
+    // 3. exact ties between crossings of different axes
     if (!irregular) {
       bool tie = false, overflow = false;
-      tie_rows<DIM, 1>(sm, nseg, lane, Sg, p64, stride, tie, overflow);
-      if constexpr (DIM > 2) tie_rows<DIM, DIM - 1>(sm, nseg, lane, Sg, p64, stride, tie, overflow);
+      tie_pass<DIM>(sm, nseg, lane, Sg, p64, tie, overflow);
       irregular = __any_sync(0xffffffffu, tie || overflow) != 0;
     }
     if (!irregular) {

@@ -6,6 +6,11 @@
 
 namespace pct {
 
+// Entries are taken 128 per warp and round: each lane issues its four col /
+// val loads (streamed with an evict-first hint, so that x keeps its place in
+// the L2), then its four x gathers, before the first product needs one.
+constexpr int kCsrUnroll = 4;
+
 __global__ void k_csr_forward(const long long* __restrict__ row_ptr, const int* __restrict__ col,
                               const float* __restrict__ val, long long row0, long long n,
                               const float* __restrict__ x, float* __restrict__ y) {
@@ -15,7 +20,21 @@ __global__ void k_csr_forward(const long long* __restrict__ row_ptr, const int* 
   long long r = row0 + w;
   long long beg = row_ptr[r], end = row_ptr[r + 1];
   float acc = 0.0f;
-  for (long long e = beg + lane; e < end; e += 32) acc = fmaf(__ldg(val + e), __ldg(x + __ldg(col + e)), acc);
+  for (long long e0 = beg + lane; e0 < end; e0 += 32 * kCsrUnroll) {
+    int c[kCsrUnroll];
+    float v[kCsrUnroll], xv[kCsrUnroll];
+#pragma unroll
+    for (int u = 0; u < kCsrUnroll; ++u) {
+      const long long e = e0 + 32 * u;
+      c[u] = e < end ? __ldcs(col + e) : -1;
+      v[u] = e < end ? __ldcs(val + e) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < kCsrUnroll; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : 0.0f;
+#pragma unroll
+    for (int u = 0; u < kCsrUnroll; ++u)
+      if (c[u] >= 0) acc = fmaf(v[u], xv[u], acc);
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if (lane == 0) y[w] = acc;
@@ -33,8 +52,19 @@ __global__ void k_csr_adjoint(const long long* __restrict__ row_ptr, const int* 
   long long beg = row_ptr[rr], end = row_ptr[rr + 1];
   // plain `red` with no memory clobber (nothing here reads g): the next
   // entries' col / val loads may be issued ahead of it
-  for (long long e = beg + lane; e < end; e += 32)
-    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(g + __ldg(col + e)), "f"(__ldg(val + e) * ri));
+  for (long long e0 = beg + lane; e0 < end; e0 += 32 * kCsrUnroll) {
+    int c[kCsrUnroll];
+    float v[kCsrUnroll];
+#pragma unroll
+    for (int u = 0; u < kCsrUnroll; ++u) {
+      const long long e = e0 + 32 * u;
+      c[u] = e < end ? __ldcs(col + e) : -1;
+      v[u] = e < end ? __ldcs(val + e) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < kCsrUnroll; ++u)
+      if (c[u] >= 0) asm volatile("red.global.add.f32 [%0], %1;" ::"l"(g + c[u]), "f"(v[u] * ri));
+  }
 }
 
 void launch_csr_forward(const long long* row_ptr, const int* col, const float* val, long long row0,
