@@ -301,8 +301,9 @@ struct FillSmem {
   float4 sf[CAP];       // send, L, merged tail of the last entry, first entry's length
   int misc[CAP];
   unsigned bits[kCross / 32 + 4];
-  unsigned char ord[CAP];
+  unsigned char ord[2 * CAP];  // a segment can start a run in each of two groups (fill_axes12)
   int aux[CAP];
+  int aux2[CAP];               // first position of each segment's axis-2 crossings (fill_axes12)
   int q[kQ];
   int qn;
   __device__ int cnt(int s, int a) const { return a == 0 ? cn[s].x : (a == 1 ? cn[s].y : cn[s].z); }
@@ -362,6 +363,32 @@ __device__ __forceinline__ void mark_starts(unsigned* bits, unsigned char* ord, 
       ord[prev + __popc(bal & lt)] = (unsigned char)(lane + 32 * h);
     }
     prev += __popc(bal);
+  }
+  __syncwarp();
+}
+
+// The same for two groups of runs, the second after the first (group g of
+// segment lane + 32 h: cnt[g][h] items from base[g][h]); ord lists the runs
+// in position order, so a segment appears once per group it has items in.
+__device__ __forceinline__ void mark_starts2(unsigned* bits, unsigned char* ord, int total, const int (&cnt)[2][2],
+                                             const int (&base)[2][2], int lane) {
+  const int nwords = (total + 31) / 32 + 1;
+  for (int w = lane; w < nwords; w += 32) bits[w] = 0u;
+  __syncwarp();
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned prev = 0;
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const bool on = cnt[g][h] > 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, on);
+      if (on) {
+        atomicOr(bits + (base[g][h] >> 5), 1u << (base[g][h] & 31));
+        ord[prev + __popc(bal & lt)] = (unsigned char)(lane + 32 * h);
+      }
+      prev += __popc(bal);
+    }
   }
   __syncwarp();
 }
@@ -817,6 +844,92 @@ __device__ __forceinline__ void fill_axis(SM& sm, int nseg, int lane, const SimD
   __syncwarp();
 }
 
+// Crossings of axes 1 and 2 in one pass (3D): every axis-1 crossing of the
+// row's segments, then every axis-2 crossing (a few per row on paths that
+// run across the slices), so that the axis-2 crossings fill the last round
+// of axis 1 and only the round that straddles the two groups takes both
+// forms.  Otherwise as fill_axis.
+template <int DIM, class SM>
+__device__ __forceinline__ void fill_axes12(SM& sm, int nseg, int lane, const SimDev* Sg, const PathF64* p64,
+                                            const FillOut& F, Kahan& wk, bool& overflow) {
+  int n[2][2] = {{0, 0}, {0, 0}}, base[2][2], t[2][2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int s = lane + 32 * h;
+    if (s < nseg) {
+      n[0][h] = sm.cn[s].y;
+      n[1][h] = sm.cn[s].z;
+    }
+  }
+  base[0][0] = warp_excl_scan(n[0][0], lane, &t[0][0]);
+  base[0][1] = warp_excl_scan(n[0][1], lane, &t[0][1]) + t[0][0];
+  const int tot1 = t[0][0] + t[0][1];
+  base[1][0] = warp_excl_scan(n[1][0], lane, &t[1][0]) + tot1;
+  base[1][1] = warp_excl_scan(n[1][1], lane, &t[1][1]) + tot1 + t[1][0];
+  const int tot = tot1 + t[1][0] + t[1][1];
+  __syncwarp();  // the previous pass has finished reading aux, bits and ord
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int s = lane + 32 * h;
+    if (s < nseg) {
+      sm.aux[s] = base[0][h];
+      sm.aux2[s] = base[1][h];
+    }
+  }
+  mark_starts2(sm.bits, sm.ord, tot, n, base, lane);
+  if (lane == 0) sm.qn = 0;
+  __syncwarp();
+  int ordbase = 0;
+  float pv = 0.f, px = 0.f;
+  for (int p0 = 0; p0 < tot; p0 += 32) {
+    const int s = seg_at(sm.bits, sm.ord, p0, lane, ordbase);
+    const int p = p0 + lane;
+    float v = 0.f, xv = 0.f;
+    if (p < tot) {
+      float4 ax[DIM];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) ax[c] = sm.ax[c][s];
+      const int4 cn = sm.cn[s], dc = sm.dc[s];
+      const float4 sf = sm.sf[s];
+      const bool second = p >= tot1;
+      const int i = p - (second ? sm.aux2[s] : sm.aux[s]);
+      bool unsure = false;
+      float ph;
+      Cross cr;
+      if (!second)
+        cr = cross_x<DIM, 1>(ax, cn, dc, sf.x, i, ph, unsure);
+      else
+        cr = cross_x<DIM, DIM - 1>(ax, cn, dc, sf.x, i, ph, unsure);
+      if (!unsure) {
+        v = fmaf(fmaxf(cr.nv - ph, 0.f), sf.y, cr.last ? sf.z : 0.f);
+        xv = put_entry_x(F, dc.w + cr.rank, cr.colv, v);
+      } else {
+        const int k = atomicAdd(&sm.qn, 1);
+        if (k < SM::kQ)
+          sm.q[k] = s | ((second ? 2 : 1) << 8) | (i << 10);
+        else
+          overflow = true;
+      }
+    }
+    wk.add(pv * px);
+    pv = v;
+    px = xv;
+  }
+  wk.add(pv * px);
+  __syncwarp();
+  const int nq = min(sm.qn, SM::kQ);
+  for (int k = lane; k < nq; k += 32) {
+    const int s = sm.q[k] & 0xff, a = (sm.q[k] >> 8) & 3, i = sm.q[k] >> 10;
+    const float4 sf = sm.sf[s];
+    const float4 axa = sm.ax[a][s];
+    const float ph = fmaf((float)i, axa.y, axa.x);
+    const Cross cr = cross_exact<DIM>(Sg, p64, s, fill_axes<DIM>(sm, s, a), i, sm.cn[s].w, sm.misc[s], sf.x);
+    const float v = fmaf(fmaxf(cr.nv - ph, 0.f), sf.y, cr.last ? sf.z : 0.f);
+    put_entry(F, sm.dc[s].w + cr.rank, cr.colv, v, wk);
+  }
+  __syncwarp();
+}
+
 // ---------------------------------------------------------------------------
 // Count: one row, the whole warp.  Sets up the interior segments (one per
 // lane), forms the per-segment counts, merges and prefix sums, looks for
@@ -930,7 +1043,6 @@ __device__ __forceinline__ bool coop_count_row(const SimDev& S, const MixArgs& M
                                                long long row, SM& sm, long long* __restrict__ counts) {
   using W = SegW<DIM>;
   const int lane = threadIdx.x & 31;
-  const GridDev& g = S.ph.g;
   const RowDF& r = M.rdf[row];
   const int nseg = r.nv - 1;
   const PathF64* p64 = M.r64 + row;
@@ -1045,8 +1157,10 @@ __device__ __forceinline__ bool coop_fill_row(const SimDev& S, const MixArgs& M,
       const PathF64* p64 = M.r64 + row;
       bool overflow = false;
       fill_axis<DIM, 0>(sm, nseg, lane, Sg, p64, F, wk, overflow);
-      fill_axis<DIM, 1>(sm, nseg, lane, Sg, p64, F, wk, overflow);
-      if constexpr (DIM > 2) fill_axis<DIM, DIM - 1>(sm, nseg, lane, Sg, p64, F, wk, overflow);
+      if constexpr (DIM > 2)
+        fill_axes12<DIM>(sm, nseg, lane, Sg, p64, F, wk, overflow);
+      else
+        fill_axis<DIM, 1>(sm, nseg, lane, Sg, p64, F, wk, overflow);
       // 2. entry 0 of every segment that does not continue the previous one
 #pragma unroll
       for (int h = 0; h < 2; ++h) {

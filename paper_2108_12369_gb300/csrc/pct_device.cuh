@@ -205,20 +205,29 @@ __device__ __forceinline__ double own_log(double x) {
 
 // Marsaglia polar method (Sec. II-B): pair of independent standard normals
 // from the stream starting at uniform j; advances j.  64 attempts at most.
+// The accepted point is found first and transformed after the loop: lanes
+// accept at different attempts, and a transform inside the loop would run
+// once per distinct attempt count in the warp (two to three times).
 __device__ __forceinline__ void normal_pair(UniformStream& us, long long& j, double& z1,
                                             double& z2) {
+  double v1 = 0.0, v2 = 0.0, s = 0.0;
+  bool ok = false;
+  for (int attempt = 0; attempt < 64; ++attempt) {
+    v1 = us.get_sym(j);  // 2 U - 1
+    v2 = us.get_sym(j + 1);
+    j += 2;
+    s = v1 * v1 + v2 * v2;
+    if (s > 0.0 && s < 1.0) {
+      ok = true;
+      break;
+    }
+  }
   z1 = 0.0;
   z2 = 0.0;
-  for (int attempt = 0; attempt < 64; ++attempt) {
-    const double v1 = us.get_sym(j), v2 = us.get_sym(j + 1);  // 2 U - 1
-    j += 2;
-    double s = v1 * v1 + v2 * v2;
-    if (s > 0.0 && s < 1.0) {
-      double f = sqrt((-2.0 * own_log(s)) / s);
-      z1 = v1 * f;
-      z2 = v2 * f;
-      return;
-    }
+  if (ok) {
+    double f = sqrt((-2.0 * own_log(s)) / s);
+    z1 = v1 * f;
+    z2 = v2 * f;
   }
 }
 
