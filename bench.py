@@ -52,6 +52,8 @@ KERNEL_FILES = {
     "f64": ["pct_f64.cu", "pct_device.cuh"],
 }
 FILL_KERNEL = {"mixed": "k_fill_mixed", "f64": "k_fill_f64"}
+# angles per block of the end-to-end leg's pct_simulate_host (9 blocks of the 3D head)
+E2E_ANGLES_PER_BLOCK = 10
 # our kernels launched per step: raster, path set-up + lead segments + count (mixed) or count (f64), 3 scan passes, fill
 LAUNCHES_PER_STEP = {"mixed": 8, "f64": 6}
 
@@ -370,10 +372,11 @@ def run_ours(args):
         del ws64
 
     # end to end through the C ABI with host buffers: angle / basis tables go
-    # up from host memory inside every call; pct_simulate_fill_host writes
-    # the row pointers, the CSR and b to pinned host memory every step (block
-    # by block through a 1 GB device staging buffer, each block's copy
-    # overlapping the next block's fill)
+    # up from host memory inside every call; pct_simulate_host counts and
+    # fills the acquisition in blocks of E2E_ANGLES_PER_BLOCK angles and
+    # writes the row pointers, the CSR and b to pinned host memory every step
+    # (through a 1 GB device staging buffer; a block's copies overlap the
+    # next block's count and fill)
     small = args.no_e2e
     del col, val  # the host path needs no device CSR
     h_rp = torch.empty(1 if small else n_rows + 1, dtype=torch.int64, pin_memory=True)
@@ -385,10 +388,9 @@ def run_ours(args):
 
     def step_host():
         pct.phantom_rasterize(ph, x)
-        pct.simulate_count(ph, geo, prec, ws, rp)
-        if int(rp[-1].item()) != nnz:
+        got = pct.simulate_host(ph, geo, prec, E2E_ANGLES_PER_BLOCK, ws, x, staging, h_rp, h_col, h_val, h_b)
+        if got != nnz:
             raise RuntimeError("nnz changed between steps")
-        pct.simulate_fill_host(ph, geo, prec, ws, rp, x, staging, h_rp, h_col, h_val, h_b)
 
     for _ in range(args.warmup if e2e_steps else 0):
         step_host()  # warm-up (first launches, first writes to the pinned pages), untimed
@@ -408,9 +410,12 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     e2e_value = total_rows * e2e_steps / e2e_s if e2e_steps else None
-    K = w["model"].get("spline_segments", 1)
-    h2d = len(w["angles"]) * 16 + (K + 1) * 32
-    d2h = (n_rows + 1) * 8 + nnz * 8 + n_rows * 4
+    K = w["model"].get("spline_segments", 1) if w["model"]["model"] == W.SPLINE else 1
+    n_blocks = -(-len(w["angles"]) // E2E_ANGLES_PER_BLOCK)
+    # per block: its angles' cos / sin, the spline basis in FP64 and double-float
+    h2d = len(w["angles"]) * 16 + n_blocks * (K + 1) * 64
+    # per block: its row pointers (one more than its rows); all entries and b
+    d2h = (n_rows + n_blocks) * 8 + nnz * 8 + n_rows * 4
 
     if rank != 0:
         if world > 1:
@@ -448,6 +453,7 @@ def run_ours(args):
         "wall_s_timed_loop": t_wall,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "api": "pct_phantom_rasterize + pct_simulate_host", "angles_per_block": E2E_ANGLES_PER_BLOCK,
                 "steps": e2e_steps, "step_ms": [round(v, 2) for v in e2e_step_ms]},
         "gpu_launches": LAUNCHES_PER_STEP[args.precision] * args.steps,
     }

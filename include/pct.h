@@ -223,6 +223,39 @@ pct_status pct_simulate_fill_host(const pct_phantom* ph, const pct_geometry* geo
                                   int64_t* row_ptr_host, int32_t* col_host, float* val_host, float* b_host,
                                   void* stream);
 
+/* Bytes of device workspace for pct_simulate_host with blocks of
+ * angles_per_block angles (>= 1): the layout of one block's simulation plus
+ * the block's row pointers. */
+pct_status pct_simulate_host_workspace_size(const pct_phantom* ph, const pct_geometry* geo, int32_t precision,
+                                            int32_t angles_per_block, size_t* bytes);
+
+/* The whole simulation into HOST memory in one call (Sec. II-C: the
+ * simulator's output is the system A, b, here for acquisitions whose CSR
+ * need not, or cannot, stay on the device).  The acquisition is taken in
+ * blocks of angles_per_block angles (the last may be shorter), each the
+ * geometry's angle block k0..k1 with first_row + k0 P, so that its rows are
+ * the acquisition's own.  Per block, on `stream`: the count and the scan
+ * into the workspace (sized by pct_simulate_host_workspace_size), the
+ * block's row pointers read back (one synchronisation per block), then the
+ * fill through staging_dev exactly as pct_simulate_fill_host does; a block's
+ * copies to the host run on two internal streams while the next block is
+ * counted and filled.  x_true_dev: the rasterised phantom (device).
+ * row_ptr_host[0..n_rows], b_host[0..n_rows) and, when the acquisition's
+ * nonzero count fits nnz_capacity, col_host / val_host[0..nnz) receive the
+ * values of pct_simulate_count + pct_simulate_fill.  *nnz_out receives the
+ * nonzero count in every case.  When it exceeds nnz_capacity the remaining
+ * blocks are only counted (col_host / val_host may be NULL; capacity 0 makes
+ * the call a count with a one-block workspace), col / val / b hold nothing
+ * defined and the call returns PCT_ENOMEM.  Host buffers should be pinned.
+ * Synchronises: on return the host buffers are complete.  EINVAL for NULL
+ * pointers, angles_per_block < 1 or a row with more entries than a staging
+ * half holds; ENOMEM for a short workspace.  Caller owns every buffer. */
+pct_status pct_simulate_host(const pct_phantom* ph, const pct_geometry* geo, int32_t precision,
+                             int32_t angles_per_block, void* workspace_dev, size_t workspace_bytes,
+                             const float* x_true_dev, void* staging_dev, size_t staging_bytes,
+                             int64_t* row_ptr_host, int32_t* col_host, float* val_host, float* b_host,
+                             int64_t nnz_capacity, int64_t* nnz_out, void* stream);
+
 /* Whole simulation: rasterises x_true, counts, reads nnz back (synchronises
  * the stream once), allocates through alloc_fn and fills.  out receives
  * device buffers owned by the caller (free them with free_fn).  On failure

@@ -335,9 +335,112 @@ extern "C" pct_status pct_simulate_fill(const pct_phantom* ph, const pct_geometr
   return cuda_check("fill launch");
 }
 
-// Phase 2 into host memory: the rows are filled block by block into two
-// device staging halves; the copy of one block to the host (on a second
-// stream) overlaps the fill of the next.
+namespace {
+
+// Device -> host streaming of filled rows: the rows are filled block by
+// block into two device staging halves; a block's copies to the host (col
+// on one stream, val and b on another: two copy engines move the block at
+// once) overlap the fill of the next block, and a half is refilled only
+// after both its copies.  Blocks continue across calls of rows(), so one
+// HostStream serves the blocks of several simulations in turn.
+struct HostStream {
+  cudaStream_t st = nullptr, cs[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fill[2] = {nullptr, nullptr}, ev_copy[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  char* base = nullptr;
+  long long half = 0, E = 0, Rb = 0, k = 0;  // k: staging blocks issued so far (half k & 1 next)
+  bool ok = true;
+
+  // each half: E col entries, E val entries, E / 16 b values (E a multiple of 64)
+  pct_status init(cudaStream_t s, void* staging, size_t staging_bytes) {
+    st = s;
+    base = (char*)staging;
+    half = (long long)(staging_bytes / 2) & ~255LL;
+    E = (long long)((double)half / 8.25) & ~63LL;
+    Rb = E / 16;
+    if (E < 64) return fail(PCT_EINVAL, "staging buffer of %zu bytes is too small", staging_bytes);
+    ok = cudaStreamCreateWithFlags(&cs[0], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&cs[1], cudaStreamNonBlocking) == cudaSuccess;
+    for (int h = 0; ok && h < 2; ++h)
+      ok = cudaEventCreateWithFlags(&ev_fill[h], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&ev_copy[h][0], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&ev_copy[h][1], cudaEventDisableTiming) == cudaSuccess;
+    return ok ? PCT_OK : cuda_check("host streaming: streams / events");
+  }
+
+  // rows [0, rows) of S (row pointers rp_dev on the device, the same values
+  // in rph on the host) into col_host / val_host (at the rows' first entry)
+  // and b_host (at their first row)
+  pct_status rows(const SimDev& S, const Layout& L, void* ws, int precision, long long rows, const long long* rp_dev,
+                  const long long* rph, const float* x, int32_t* col_host, float* val_host, float* b_host) {
+    long long r0 = 0;
+    bool first = true;
+    while (ok && r0 < rows) {
+      const long long nz0 = rph[r0];
+      // the longest block from r0 whose entries and rows fit one half
+      long long r1 = (long long)(std::upper_bound(rph + r0, rph + rows + 1, nz0 + E) - rph) - 1;
+      r1 = std::min(std::min(r1, r0 + Rb), rows);
+      if (r1 <= r0)
+        return fail(PCT_EINVAL, "staging buffer cannot hold row %lld (%lld entries)", r0, rph[r0 + 1] - nz0);
+      const long long nz1 = rph[r1];
+      const int h = (int)(k & 1);
+      int* col_s = (int*)(base + h * half);
+      float* val_s = (float*)(base + h * half + 4 * E);
+      float* b_s = (float*)(base + h * half + 8 * E);
+      if (k >= 2)
+        ok = cudaStreamWaitEvent(st, ev_copy[h][0], 0) == cudaSuccess &&
+             cudaStreamWaitEvent(st, ev_copy[h][1], 0) == cudaSuccess;
+      if (!ok) break;  // never refill a half whose copies may still be running
+      if (precision == PCT_PREC_F64)  // col / val by CSR position: bases moved back by nz0 (host arithmetic)
+        launch_fill_f64(S, r0, r1 - r0, rp_dev + r0, x, (int*)((uintptr_t)col_s - sizeof(int) * (uintptr_t)nz0),
+                        (float*)((uintptr_t)val_s - sizeof(float) * (uintptr_t)nz0), b_s, st);
+      else
+        launch_fill_mixed(S, (const char*)ws + L.basis32, L.rows, (const char*)ws + L.rec, rp_dev, x, col_s, val_s,
+                          b_s, (char*)ws + L.args, st, r0, r1, nz0, first, precision == PCT_PREC_MIXED_LEAN);
+      first = false;
+      ok = ok && cudaGetLastError() == cudaSuccess && cudaEventRecord(ev_fill[h], st) == cudaSuccess &&
+           cudaStreamWaitEvent(cs[0], ev_fill[h], 0) == cudaSuccess &&
+           cudaStreamWaitEvent(cs[1], ev_fill[h], 0) == cudaSuccess;
+      if (ok && nz1 > nz0)
+        ok = cudaMemcpyAsync(col_host + nz0, col_s, 4 * (size_t)(nz1 - nz0), cudaMemcpyDeviceToHost, cs[0]) ==
+                 cudaSuccess &&
+             cudaMemcpyAsync(val_host + nz0, val_s, 4 * (size_t)(nz1 - nz0), cudaMemcpyDeviceToHost, cs[1]) ==
+                 cudaSuccess;
+      ok = ok &&
+           cudaMemcpyAsync(b_host + r0, b_s, 4 * (size_t)(r1 - r0), cudaMemcpyDeviceToHost, cs[1]) == cudaSuccess &&
+           cudaEventRecord(ev_copy[h][0], cs[0]) == cudaSuccess && cudaEventRecord(ev_copy[h][1], cs[1]) == cudaSuccess;
+      ++k;
+      r0 = r1;
+    }
+    return ok ? PCT_OK : PCT_ECUDA;
+  }
+
+  // waits for every copy and fill; the CUDA error, if any
+  pct_status finish(const char* what) {
+    ok = ok && (!cs[0] || cudaStreamSynchronize(cs[0]) == cudaSuccess) &&
+         (!cs[1] || cudaStreamSynchronize(cs[1]) == cudaSuccess) && cudaStreamSynchronize(st) == cudaSuccess;
+    if (ok) return PCT_OK;
+    const pct_status e = cuda_check(what);
+    return e != PCT_OK ? e : fail(PCT_ECUDA, "%s: a CUDA call failed", what);
+  }
+
+  ~HostStream() {
+    for (int c = 0; c < 2; ++c)
+      if (cs[c]) cudaStreamSynchronize(cs[c]);
+    if (st) cudaStreamSynchronize(st);
+    for (int h = 0; h < 2; ++h) {
+      if (ev_fill[h]) cudaEventDestroy(ev_fill[h]);
+      for (int c = 0; c < 2; ++c)
+        if (ev_copy[h][c]) cudaEventDestroy(ev_copy[h][c]);
+    }
+    for (int c = 0; c < 2; ++c)
+      if (cs[c]) cudaStreamDestroy(cs[c]);
+  }
+};
+
+}  // namespace
+
+// Phase 2 into host memory: the rows go through the staging halves as
+// HostStream describes.
 extern "C" pct_status pct_simulate_fill_host(const pct_phantom* ph, const pct_geometry* g, int32_t precision,
                                              void* ws, size_t ws_bytes, const int64_t* row_ptr_dev,
                                              const float* x, void* staging, size_t staging_bytes,
@@ -355,95 +458,126 @@ extern "C" pct_status pct_simulate_fill_host(const pct_phantom* ph, const pct_ge
   Layout L;
   rc = make_sim(ph, g, precision, ws, ws_bytes, st, S, L);
   if (rc != PCT_OK) return rc;
-  // each half: E col entries, E val entries, E / 16 b values (E a multiple of 64)
-  const long long half = (long long)(staging_bytes / 2) & ~255LL;
-  const long long E = (long long)((double)half / 8.25) & ~63LL;
-  const long long Rb = E / 16;
   if (cudaMemcpyAsync(row_ptr_host, row_ptr_dev, sizeof(int64_t) * (size_t)(L.rows + 1), cudaMemcpyDeviceToHost,
                       st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return cuda_check("pct_simulate_fill_host: row pointers");
   if (L.rows == 0) return PCT_OK;
-  if (E < 64) return fail(PCT_EINVAL, "staging buffer of %zu bytes is too small", staging_bytes);
   const long long* rph = (const long long*)row_ptr_host;
   if (rph[L.rows] > 0 && (!col_host || !val_host))
     return fail(PCT_EINVAL, "pct_simulate_fill_host: NULL col_host or val_host for %lld nonzeros", rph[L.rows]);
-  // two copy streams (col on one, val and b on the other: two copy engines
-  // move the block at once); a half is refilled only after both its copies
-  cudaStream_t cs[2] = {nullptr, nullptr};
-  cudaEvent_t ev_fill[2] = {nullptr, nullptr}, ev_copy[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-  auto cleanup = [&]() {
-    for (int c = 0; c < 2; ++c)
-      if (cs[c]) cudaStreamSynchronize(cs[c]);
-    cudaStreamSynchronize(st);
-    for (int h = 0; h < 2; ++h) {
-      if (ev_fill[h]) cudaEventDestroy(ev_fill[h]);
-      for (int c = 0; c < 2; ++c)
-        if (ev_copy[h][c]) cudaEventDestroy(ev_copy[h][c]);
-    }
-    for (int c = 0; c < 2; ++c)
-      if (cs[c]) cudaStreamDestroy(cs[c]);
-  };
-  bool ok = cudaStreamCreateWithFlags(&cs[0], cudaStreamNonBlocking) == cudaSuccess &&
-            cudaStreamCreateWithFlags(&cs[1], cudaStreamNonBlocking) == cudaSuccess;
-  for (int h = 0; ok && h < 2; ++h)
-    ok = cudaEventCreateWithFlags(&ev_fill[h], cudaEventDisableTiming) == cudaSuccess &&
-         cudaEventCreateWithFlags(&ev_copy[h][0], cudaEventDisableTiming) == cudaSuccess &&
-         cudaEventCreateWithFlags(&ev_copy[h][1], cudaEventDisableTiming) == cudaSuccess;
-  if (!ok) {
-    cleanup();
-    return cuda_check("pct_simulate_fill_host: streams / events");
-  }
-  char* base = (char*)staging;
-  long long r0 = 0;
-  for (int k = 0; ok && r0 < L.rows; ++k) {
-    const long long nz0 = rph[r0];
-    // the longest block from r0 whose entries and rows fit one half
-    long long r1 = (long long)(std::upper_bound(rph + r0, rph + L.rows + 1, nz0 + E) - rph) - 1;
-    r1 = std::min(std::min(r1, r0 + Rb), (long long)L.rows);
-    if (r1 <= r0) {
-      cleanup();
-      return fail(PCT_EINVAL, "staging buffer of %zu bytes cannot hold row %lld (%lld entries)", staging_bytes,
-                  r0, rph[r0 + 1] - nz0);
-    }
-    const long long nz1 = rph[r1];
-    const int h = k & 1;
-    int* col_s = (int*)(base + h * half);
-    float* val_s = (float*)(base + h * half + 4 * E);
-    float* b_s = (float*)(base + h * half + 8 * E);
-    if (k >= 2)
-      ok = cudaStreamWaitEvent(st, ev_copy[h][0], 0) == cudaSuccess &&
-           cudaStreamWaitEvent(st, ev_copy[h][1], 0) == cudaSuccess;
-    if (!ok) break;  // never refill a half whose copies may still be running
-    if (precision == PCT_PREC_F64)  // col / val by CSR position: bases moved back by nz0 (host arithmetic)
-      launch_fill_f64(S, r0, r1 - r0, (const long long*)row_ptr_dev + r0, x,
-                      (int*)((uintptr_t)col_s - sizeof(int) * (uintptr_t)nz0),
-                      (float*)((uintptr_t)val_s - sizeof(float) * (uintptr_t)nz0), b_s, st);
+  HostStream hs;
+  if ((rc = hs.init(st, staging, staging_bytes)) != PCT_OK) return rc;
+  rc = hs.rows(S, L, ws, precision, L.rows, (const long long*)row_ptr_dev, rph, x, col_host, val_host, b_host);
+  const pct_status fin = hs.finish("pct_simulate_fill_host");
+  return rc == PCT_EINVAL ? rc : fin;
+}
+
+namespace {
+
+// the geometry of angles [a0, a1) of g: the acquisition's own rows
+pct_geometry angle_block(const pct_geometry* g, int a0, int a1) {
+  pct_geometry b = *g;
+  b.angles_rad = g->angles_rad ? g->angles_rad + a0 : nullptr;
+  b.n_angles = a1 - a0;
+  b.first_row = g->first_row + (int64_t)a0 * g->paths_per_angle;
+  return b;
+}
+
+// one block's layout (the largest block) and the offset of its row pointers
+size_t host_block_layout(const pct_phantom* ph, const pct_geometry* g, int precision, int apb, size_t* rp_off) {
+  const int n = std::min(apb, g->n_angles);
+  const pct_geometry b = angle_block(g, 0, n);
+  const Layout L = layout_of(ph, &b, precision);
+  *rp_off = L.total;
+  return L.total + align256(sizeof(long long) * (size_t)(L.rows + 1));
+}
+
+}  // namespace
+
+extern "C" pct_status pct_simulate_host_workspace_size(const pct_phantom* ph, const pct_geometry* g, int32_t precision,
+                                                       int32_t angles_per_block, size_t* bytes) {
+  if (!bytes) return fail(PCT_EINVAL, "bytes is NULL");
+  pct_status rc = check_geometry(ph, g, precision);
+  if (rc != PCT_OK) return rc;
+  if (angles_per_block < 1) return fail(PCT_EINVAL, "angles_per_block = %d must be >= 1", angles_per_block);
+  size_t off;
+  *bytes = host_block_layout(ph, g, precision, angles_per_block, &off);
+  return PCT_OK;
+}
+
+extern "C" pct_status pct_simulate_host(const pct_phantom* ph, const pct_geometry* g, int32_t precision,
+                                        int32_t angles_per_block, void* ws, size_t ws_bytes, const float* x,
+                                        void* staging, size_t staging_bytes, int64_t* row_ptr_host, int32_t* col_host,
+                                        float* val_host, float* b_host, int64_t nnz_capacity, int64_t* nnz_out,
+                                        void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  // argument checks first (host only)
+  pct_status rc = check_geometry(ph, g, precision);
+  if (rc != PCT_OK) return rc;
+  if (angles_per_block < 1) return fail(PCT_EINVAL, "angles_per_block = %d must be >= 1", angles_per_block);
+  if (!row_ptr_host || !nnz_out) return fail(PCT_EINVAL, "pct_simulate_host: NULL row_ptr_host or nnz_out");
+  if (nnz_capacity < 0) return fail(PCT_EINVAL, "nnz_capacity must be >= 0");
+  const long long rows = (long long)g->n_angles * g->paths_per_angle;
+  if (rows > 0 && (!x || !b_host || !staging)) return fail(PCT_EINVAL, "pct_simulate_host: NULL argument");
+  if ((uintptr_t)staging % 256 != 0) return fail(PCT_EINVAL, "staging buffer must be 256-byte aligned");
+  if (nnz_capacity > 0 && (!col_host || !val_host))
+    return fail(PCT_EINVAL, "pct_simulate_host: NULL col_host or val_host with nnz_capacity %lld",
+                (long long)nnz_capacity);
+  *nnz_out = 0;
+  row_ptr_host[0] = 0;
+  if (rows == 0) return PCT_OK;
+  size_t rp_off;
+  const size_t need = host_block_layout(ph, g, precision, angles_per_block, &rp_off);
+  if (!ws || ws_bytes < need)
+    return fail(PCT_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed", ws_bytes, need);
+  long long* rp_dev = (long long*)((char*)ws + rp_off);
+  HostStream hs;
+  if ((rc = hs.init(st, staging, staging_bytes)) != PCT_OK) return rc;
+  long long nz = 0;
+  bool filling = true;
+  for (int a0 = 0; a0 < g->n_angles && rc == PCT_OK; a0 += angles_per_block) {
+    const int a1 = std::min(a0 + angles_per_block, g->n_angles);
+    const pct_geometry gb = angle_block(g, a0, a1);
+    SimDev S;
+    Layout L;
+    if ((rc = make_sim(ph, &gb, precision, ws, rp_off, st, S, L)) != PCT_OK) break;
+    const long long r0 = (long long)a0 * g->paths_per_angle;
+    if (L.rows == 0) continue;
+    // count and scan of the block (after the previous block's fills on st)
+    if (precision == PCT_PREC_F64)
+      launch_count_f64(S, 0, L.rows, rp_dev + 1, st);
     else
-      launch_fill_mixed(S, (const char*)ws + L.basis32, L.rows, (const char*)ws + L.rec,
-                        (const long long*)row_ptr_dev, x, col_s, val_s, b_s, (char*)ws + L.args, st, r0, r1, nz0,
-                        k == 0, precision == PCT_PREC_MIXED_LEAN);
-    ok = ok && cudaGetLastError() == cudaSuccess && cudaEventRecord(ev_fill[h], st) == cudaSuccess &&
-         cudaStreamWaitEvent(cs[0], ev_fill[h], 0) == cudaSuccess &&
-         cudaStreamWaitEvent(cs[1], ev_fill[h], 0) == cudaSuccess;
-    if (ok && nz1 > nz0)
-      ok = cudaMemcpyAsync(col_host + nz0, col_s, 4 * (size_t)(nz1 - nz0), cudaMemcpyDeviceToHost, cs[0]) ==
-               cudaSuccess &&
-           cudaMemcpyAsync(val_host + nz0, val_s, 4 * (size_t)(nz1 - nz0), cudaMemcpyDeviceToHost, cs[1]) ==
-               cudaSuccess;
-    ok = ok &&
-         cudaMemcpyAsync(b_host + r0, b_s, 4 * (size_t)(r1 - r0), cudaMemcpyDeviceToHost, cs[1]) == cudaSuccess &&
-         cudaEventRecord(ev_copy[h][0], cs[0]) == cudaSuccess && cudaEventRecord(ev_copy[h][1], cs[1]) == cudaSuccess;
-    r0 = r1;
+      launch_count_mixed(S, (const char*)ws + L.basis32, L.rows, (char*)ws + L.rec, rp_dev + 1, (char*)ws + L.args,
+                         st, precision == PCT_PREC_MIXED_LEAN);
+    if ((rc = cuda_check("pct_simulate_host: count launch")) != PCT_OK) break;
+    launch_scan_rowptr(rp_dev, L.rows, (long long*)((char*)ws + L.partial), st);
+    // the block's row pointers, local to the block, where its global ones go
+    long long* rph = (long long*)row_ptr_host + r0;
+    if (cudaMemcpyAsync(rph, rp_dev, sizeof(long long) * (size_t)(L.rows + 1), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      rc = cuda_check("pct_simulate_host: row pointers");
+      if (rc == PCT_OK) rc = fail(PCT_ECUDA, "pct_simulate_host: row pointers");
+      break;
+    }
+    const long long nb = rph[L.rows];
+    filling = filling && nz + nb <= nnz_capacity;
+    if (filling) {
+      rc = hs.rows(S, L, ws, precision, L.rows, rp_dev, rph, x, col_host + nz, val_host + nz, b_host + r0);
+      if (rc != PCT_OK) break;
+    }
+    // global row pointers (the fills above have read the local ones)
+    for (long long i = 0; i <= L.rows; ++i) rph[i] += nz;
+    nz += nb;
   }
-  ok = ok && cudaStreamSynchronize(cs[0]) == cudaSuccess && cudaStreamSynchronize(cs[1]) == cudaSuccess &&
-       cudaStreamSynchronize(st) == cudaSuccess;
-  if (!ok) {
-    const pct_status e = cuda_check("pct_simulate_fill_host");
-    cleanup();
-    return e != PCT_OK ? e : fail(PCT_ECUDA, "pct_simulate_fill_host: a CUDA call failed");
-  }
-  cleanup();
+  const pct_status fin = hs.finish("pct_simulate_host");
+  if (rc == PCT_OK) rc = fin;
+  if (rc != PCT_OK) return rc == PCT_ECUDA && fin != PCT_OK ? fin : rc;
+  *nnz_out = nz;
+  if (!filling)
+    return fail(PCT_ENOMEM, "pct_simulate_host: %lld nonzeros exceed nnz_capacity %lld (row pointers complete)", nz,
+                (long long)nnz_capacity);
   return PCT_OK;
 }
 

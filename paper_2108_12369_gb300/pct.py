@@ -72,7 +72,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 # every symbol include/pct.h declares
 EXPORTS = ["pct_phantom_create", "pct_phantom_destroy", "pct_phantom_nvox", "pct_phantom_rasterize",
            "pct_simulate_workspace_size", "pct_simulate_count", "pct_simulate_fill", "pct_simulate_fill_host",
-           "pct_simulate",
+           "pct_simulate_host_workspace_size", "pct_simulate_host", "pct_simulate",
            "pct_projector_workspace_size", "pct_forward", "pct_adjoint", "pct_batch_workspace_size", "pct_batch_create",
            "pct_batch_count", "pct_batch_nnz", "pct_batch_fill", "pct_batch_params", "pct_batch_destroy",
            "pct_scan_counts_static", "pct_sap_workspace_size", "pct_sap", "pct_csr_file_create",
@@ -102,6 +102,9 @@ def lib():
                                   C.c_int),
             "pct_simulate_fill_host": ([vp, P(Geometry), C.c_int32, vp, C.c_size_t, vp, vp, vp, C.c_size_t, vp, vp,
                                         vp, vp, vp], C.c_int),
+            "pct_simulate_host_workspace_size": ([vp, P(Geometry), C.c_int32, C.c_int32, P(C.c_size_t)], C.c_int),
+            "pct_simulate_host": ([vp, P(Geometry), C.c_int32, C.c_int32, vp, C.c_size_t, vp, vp, C.c_size_t, vp, vp,
+                                   vp, vp, C.c_int64, P(C.c_int64), vp], C.c_int),
             "pct_simulate": ([vp, P(Geometry), C.c_int32, ALLOC_FN, FREE_FN, vp, P(Csr), vp], C.c_int),
             "pct_projector_workspace_size": ([vp, P(Geometry), C.c_int32, C.c_int64, P(C.c_size_t)],
                                              C.c_int),
@@ -238,6 +241,32 @@ def simulate_fill_host(ph, geo, precision, workspace, row_ptr, x_true, staging, 
                                         workspace.numel() * workspace.element_size(), _ptr(row_ptr),
                                         _ptr(x_true), _ptr(staging), staging.numel() * staging.element_size(),
                                         _ptr(row_ptr_h), _ptr(col_h), _ptr(val_h), _ptr(b_h), _stream(stream)))
+
+
+def simulate_host_workspace_size(ph: Phantom, geo: GeometryArgs, precision: int, angles_per_block: int) -> int:
+    n = C.c_size_t()
+    _check(lib().pct_simulate_host_workspace_size(ph.handle, C.byref(geo.c), precision, int(angles_per_block),
+                                                  C.byref(n)))
+    return n.value
+
+
+def simulate_host(ph, geo, precision, angles_per_block, workspace, x_true, staging, row_ptr_h, col_h, val_h, b_h,
+                  stream=None) -> int:
+    """The whole simulation into host tensors (pinned for overlapped copies),
+    angle block by angle block; returns nnz.  col_h / val_h hold the CSR
+    entries when nnz <= their length; otherwise only row_ptr_h is complete
+    (col_h / val_h may then be None, e.g. to learn nnz with a small
+    workspace)."""
+    cap = 0 if col_h is None else min(col_h.numel(), val_h.numel())
+    nnz = C.c_int64()
+    st = lib().pct_simulate_host(ph.handle, C.byref(geo.c), precision, int(angles_per_block), _ptr(workspace),
+                                 workspace.numel() * workspace.element_size(), _ptr(x_true), _ptr(staging),
+                                 staging.numel() * staging.element_size(), _ptr(row_ptr_h), _ptr(col_h), _ptr(val_h),
+                                 _ptr(b_h), cap, C.byref(nnz), _stream(stream))
+    if st == ENOMEM and nnz.value > cap:
+        return nnz.value  # the capacity case: row pointers complete, entries not written
+    _check(st)
+    return nnz.value
 
 
 def simulate(ph: Phantom, geo: GeometryArgs, precision: int = PREC_MIXED, stream=None, device="cuda"):

@@ -113,6 +113,43 @@ def test_fill_host_validates_before_any_device_work(pct):
     assert st == pct.EINVAL and b"aligned" in L.pct_last_error()
 
 
+def test_simulate_host_validates_before_any_device_work(pct):
+    """pct_simulate_host checks its arguments and workspace on the host; its
+    workspace is one angle block's (no GPU needed)."""
+    w = W.head_3d_spline(n_angles=9, paths_per_angle=100, n=(32, 32, 24))
+    ph, geo = pct.Phantom(w["phantom"]), pct.GeometryArgs(w)
+    L = pct.lib()
+    sizes = [pct.simulate_host_workspace_size(ph, geo, pct.PREC_MIXED, k) for k in (1, 3, 9, 20)]
+    assert sizes[0] < sizes[1] < sizes[2] == sizes[3]
+    assert sizes[1] < pct.simulate_workspace_size(ph, geo, pct.PREC_MIXED)
+    with pytest.raises(pct.PctError) as e:
+        pct.simulate_host_workspace_size(ph, geo, pct.PREC_MIXED, 0)
+    assert e.value.status == pct.EINVAL
+    buf = (C.c_int64 * 64)()
+    p = C.cast(buf, C.c_void_p)
+    nnz = C.c_int64(-1)
+
+    stg = C.c_void_p((p.value + 255) // 256 * 256)  # fake device staging address (never dereferenced)
+    odd = C.c_void_p(stg.value + 8)  # not 256-byte aligned
+
+    def call(apb, ws_bytes, x, staging, rp, col, cap, out, why):
+        st = L.pct_simulate_host(ph.handle, C.byref(geo.c), pct.PREC_MIXED, apb, p, ws_bytes, x, staging, 1 << 20,
+                                 rp, col, col, p, cap, out, None)
+        assert why.encode() in L.pct_last_error(), (why, L.pct_last_error())
+        return st
+    assert call(0, 1 << 40, p, stg, p, p, 10, C.byref(nnz), "angles_per_block") == pct.EINVAL
+    assert call(2, 1 << 40, p, stg, None, p, 10, C.byref(nnz), "NULL row_ptr_host") == pct.EINVAL
+    assert call(2, 1 << 40, p, stg, p, p, 10, None, "nnz_out") == pct.EINVAL
+    assert call(2, 1 << 40, p, stg, p, p, -1, C.byref(nnz), "nnz_capacity") == pct.EINVAL
+    assert call(2, 1 << 40, None, stg, p, p, 10, C.byref(nnz), "NULL argument") == pct.EINVAL
+    assert call(2, 1 << 40, p, stg, p, None, 10, C.byref(nnz), "NULL col_host") == pct.EINVAL
+    assert call(2, 1 << 40, p, odd, p, p, 10, C.byref(nnz), "aligned") == pct.EINVAL
+    need = pct.simulate_host_workspace_size(ph, geo, pct.PREC_MIXED, 2)
+    buf[0] = 7
+    assert call(2, need - 1, p, stg, p, None, 0, C.byref(nnz), "workspace") == pct.ENOMEM
+    assert nnz.value == 0 and buf[0] == 0
+
+
 class _FakeAllocator:
     """Allocator callbacks that hand out fake, never-dereferenced addresses and
     return NULL on call number `fail_at` (1-based); counts every call."""
