@@ -465,10 +465,14 @@ __device__ __forceinline__ bool seg_setup_fast(const GridDev& g, const GridDF& g
     s.step[a] = Dh > 0.f ? 1 : -1;
     s.idx[a] = i;
     s.kn[a] = Dh > 0.f ? i + 1 : i;
-    w.ph0[a] = (Dh > 0.f ? (h - r) : r) / aD;
-    w.hv[a] = h / aD;
+    // one correctly rounded reciprocal for the three quotients: each is
+    // within about 1 u of the quotient of its operands (a division: 1/2 u);
+    // the bounds built on them carry 4 u and more
+    const float raD = __frcp_rn(aD);
+    w.ph0[a] = (Dh > 0.f ? (h - r) : r) * raD;
+    w.hv[a] = h * raD;
     w.kf[a] = 0.f;
-    w.e0[a] = (2.f * mr) / aD + 4.f * kU32 * w.ph0[a];
+    w.e0[a] = (2.f * mr) * raD + 4.f * kU32 * w.ph0[a];
   }
   s.L = sqrtf(L2);
   s.in = Ev{-1, 0};
