@@ -223,6 +223,19 @@ pct_status pct_simulate_fill_host(const pct_phantom* ph, const pct_geometry* geo
                                   int64_t* row_ptr_host, int32_t* col_host, float* val_host, float* b_host,
                                   void* stream);
 
+/* The fill's row check (Sec. II-C: row i of A holds exactly the entries of
+ * proton i's path).  Every fill compares, per row, the entries it writes with
+ * the range row_ptr gives the row; stores never leave that range, and a row
+ * whose counts differ (a row_ptr that is not the count of the same
+ * arguments and workspace) is counted in the workspace's first word, which
+ * pct_simulate_count and pct_simulate_host zero.  This call synchronises
+ * `stream` and returns that count in *mismatched_rows (0 for a consistent
+ * fill).  pct_simulate, pct_simulate_fill_host and pct_simulate_host make
+ * the same check themselves and return PCT_EINVAL when rows disagree.
+ * The batch calls do not report it (their row pointers come from their own
+ * count). */
+pct_status pct_simulate_check(const void* workspace_dev, int64_t* mismatched_rows, void* stream);
+
 /* Bytes of device workspace for pct_simulate_host with blocks of
  * angles_per_block angles (>= 1): the layout of one block's simulation plus
  * the block's row pointers. */

@@ -139,7 +139,7 @@ extern "C" pct_status pct_phantom_rasterize(const pct_phantom* ph, float* x, voi
 namespace {
 
 struct Layout {
-  size_t cs, basis, basis32, partial, args, rec, total;
+  size_t status, cs, basis, basis32, partial, args, rec, total;
   long long rows;
   int K;
 };
@@ -182,6 +182,8 @@ Layout layout_of(const pct_phantom* ph, const pct_geometry* g, int precision, lo
   L.rows = (long long)g->n_angles * g->paths_per_angle;
   L.K = (g->model.model == PCT_PATH_SPLINE) ? g->model.spline_segments : 1;
   size_t off = 0;
+  L.status = off;  // first: the same place in the workspace for every geometry
+  off = align256(off + 2 * sizeof(unsigned long long));
   L.cs = off;
   off = align256(off + sizeof(double2) * (size_t)(g->n_angles > 0 ? g->n_angles : 1));
   L.basis = off;
@@ -255,6 +257,7 @@ pct_status make_sim(const pct_phantom* ph, const pct_geometry* g, int precision,
   char* base = (char*)ws;
   S.cs = (const double2*)(base + L.cs);
   S.basis = (const Basis4*)(base + L.basis);
+  S.status = (unsigned long long*)(base + L.status);
 
   std::vector<double2> cs((size_t)(g->n_angles > 0 ? g->n_angles : 1));
   for (int k = 0; k < g->n_angles; ++k) {
@@ -307,6 +310,7 @@ extern "C" pct_status pct_simulate_count(const pct_phantom* ph, const pct_geomet
   if (rc != PCT_OK) return rc;
   if (!row_ptr) return fail(PCT_EINVAL, "row_ptr is NULL");
   long long* rp = (long long*)row_ptr;
+  if (cudaMemsetAsync(S.status, 0, sizeof(unsigned long long), st) != cudaSuccess) return cuda_check("count");
   if (precision == PCT_PREC_F64)
     launch_count_f64(S, 0, L.rows, rp + 1, st);
   else
@@ -336,6 +340,22 @@ extern "C" pct_status pct_simulate_fill(const pct_phantom* ph, const pct_geometr
 }
 
 namespace {
+
+// rows whose fill disagreed with row_ptr since the last count (synchronises st)
+pct_status read_mismatch(const void* ws, cudaStream_t st, unsigned long long* rows) {
+  *rows = 0;
+  if (cudaMemcpyAsync(rows, ws, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return cuda_check("reading the fill's row check");
+  return PCT_OK;
+}
+
+pct_status mismatch_error(const char* what, unsigned long long rows) {
+  return fail(PCT_EINVAL,
+              "%s: %llu rows received a different number of entries than row_ptr gives them (row_ptr is not the "
+              "count of these arguments and workspace)",
+              what, rows);
+}
 
 // Device -> host streaming of filled rows: the rows are filled block by
 // block into two device staging halves; a block's copies to the host (col
@@ -470,7 +490,11 @@ extern "C" pct_status pct_simulate_fill_host(const pct_phantom* ph, const pct_ge
   if ((rc = hs.init(st, staging, staging_bytes)) != PCT_OK) return rc;
   rc = hs.rows(S, L, ws, precision, L.rows, (const long long*)row_ptr_dev, rph, x, col_host, val_host, b_host);
   const pct_status fin = hs.finish("pct_simulate_fill_host");
-  return rc == PCT_EINVAL ? rc : fin;
+  if (rc == PCT_EINVAL) return rc;
+  if (fin != PCT_OK) return fin;
+  unsigned long long bad;
+  if ((rc = read_mismatch(ws, st, &bad)) != PCT_OK) return rc;
+  return bad ? mismatch_error("pct_simulate_fill_host", bad) : PCT_OK;
 }
 
 namespace {
@@ -532,6 +556,8 @@ extern "C" pct_status pct_simulate_host(const pct_phantom* ph, const pct_geometr
   if (!ws || ws_bytes < need)
     return fail(PCT_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed", ws_bytes, need);
   long long* rp_dev = (long long*)((char*)ws + rp_off);
+  if (cudaMemsetAsync(ws, 0, sizeof(unsigned long long), st) != cudaSuccess)
+    return cuda_check("pct_simulate_host: row check");
   HostStream hs;
   if ((rc = hs.init(st, staging, staging_bytes)) != PCT_OK) return rc;
   long long nz = 0;
@@ -578,7 +604,17 @@ extern "C" pct_status pct_simulate_host(const pct_phantom* ph, const pct_geometr
   if (!filling)
     return fail(PCT_ENOMEM, "pct_simulate_host: %lld nonzeros exceed nnz_capacity %lld (row pointers complete)", nz,
                 (long long)nnz_capacity);
-  return PCT_OK;
+  unsigned long long bad;
+  if ((rc = read_mismatch(ws, st, &bad)) != PCT_OK) return rc;
+  return bad ? mismatch_error("pct_simulate_host", bad) : PCT_OK;
+}
+
+extern "C" pct_status pct_simulate_check(const void* ws, int64_t* mismatched_rows, void* stream) {
+  if (!ws || !mismatched_rows) return fail(PCT_EINVAL, "pct_simulate_check: NULL argument");
+  unsigned long long bad;
+  const pct_status rc = read_mismatch(ws, (cudaStream_t)stream, &bad);
+  *mismatched_rows = (int64_t)bad;
+  return rc;
 }
 
 extern "C" pct_status pct_simulate(const pct_phantom* ph, const pct_geometry* g, int32_t precision,
@@ -634,9 +670,10 @@ extern "C" pct_status pct_simulate(const pct_phantom* ph, const pct_geometry* g,
     cleanup();
     return rc;
   }
-  if (cudaStreamSynchronize(st) != cudaSuccess) {
+  unsigned long long bad;
+  if ((rc = read_mismatch(ws, st, &bad)) != PCT_OK || (bad && (rc = mismatch_error("pct_simulate", bad)) != PCT_OK)) {
     cleanup();
-    return cuda_check("fill");
+    return rc;
   }
   free_fn(ws, ctx);
   *out = c;

@@ -300,10 +300,16 @@ struct FillSmem {
   int4 dc[CAP];         // signed column step per axis (x, y, z), first entry's CSR slot + 1 (w)
   float4 sf[CAP];       // send, L, merged tail of the last entry, first entry's length
   int misc[CAP];
+  // the two passes' positions (fill_plan): per pass the bitmap of run
+  // starts and the run -> segment map; per segment its first position in
+  // the axis-0, axis-1 and axis-2 groups
   unsigned bits[kCross / 32 + 4];
-  unsigned char ord[2 * CAP];  // a segment can start a run in each of two groups (fill_axes12)
+  unsigned bits1[kCross / 32 + 4];
+  unsigned char ord[CAP];
+  unsigned char ord1[2 * CAP];  // a segment can start a run in each of pass 1's two groups
   int aux[CAP];
-  int aux2[CAP];               // first position of each segment's axis-2 crossings (fill_axes12)
+  int aux1[CAP];
+  int aux2[CAP];
   int q[kQ];
   int qn;
   __device__ int cnt(int s, int a) const { return a == 0 ? cn[s].x : (a == 1 ? cn[s].y : cn[s].z); }
@@ -363,32 +369,6 @@ __device__ __forceinline__ void mark_starts(unsigned* bits, unsigned char* ord, 
       ord[prev + __popc(bal & lt)] = (unsigned char)(lane + 32 * h);
     }
     prev += __popc(bal);
-  }
-  __syncwarp();
-}
-
-// The same for two groups of runs, the second after the first (group g of
-// segment lane + 32 h: cnt[g][h] items from base[g][h]); ord lists the runs
-// in position order, so a segment appears once per group it has items in.
-__device__ __forceinline__ void mark_starts2(unsigned* bits, unsigned char* ord, int total, const int (&cnt)[2][2],
-                                             const int (&base)[2][2], int lane) {
-  const int nwords = (total + 31) / 32 + 1;
-  for (int w = lane; w < nwords; w += 32) bits[w] = 0u;
-  __syncwarp();
-  const unsigned lt = (1u << lane) - 1u;
-  unsigned prev = 0;
-#pragma unroll
-  for (int g = 0; g < 2; ++g) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const bool on = cnt[g][h] > 0;
-      const unsigned bal = __ballot_sync(0xffffffffu, on);
-      if (on) {
-        atomicOr(bits + (base[g][h] >> 5), 1u << (base[g][h] & 31));
-        ord[prev + __popc(bal & lt)] = (unsigned char)(lane + 32 * h);
-      }
-      prev += __popc(bal);
-    }
   }
   __syncwarp();
 }
@@ -458,7 +438,10 @@ static __device__ __noinline__ void walk_row_lane0(const SimDev* Sg, MixArgs M, 
     fs.constant = S.md.chord == PCT_CHORD_CONSTANT;
     fs.hconst = (float)S.ph.g.h[0];
     walk_row_df<DIM, true>(S, M, Sg, nullptr, r, p64, lane == 0, fs);
-    if (lane == 0) b[row] = fs.k.sum * r.fac;
+    if (lane == 0) {
+      b[row] = fs.k.sum * r.fac;
+      if (fs.pos != fs.end) note_row_mismatch(S);
+    }
   } else {
     CountSinkM cs{0};
     walk_row_df<DIM, false>(S, M, Sg, nullptr, r, p64, lane == 0, cs);
@@ -631,18 +614,6 @@ __device__ __forceinline__ int pass_starts(SM& sm, int nseg, int lane, const int
   return t0 + t1;
 }
 
-// the crossings of axis A
-template <int A, class SM>
-__device__ __forceinline__ int axis_starts(SM& sm, int nseg, int lane) {
-  int n[2] = {0, 0};
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int s = lane + 32 * h;
-    if (s < nseg) n[h] = sm.cnt(s, A);
-  }
-  return pass_starts(sm, nseg, lane, n);
-}
-
 // Exact ties between crossings of different axes, every pair of axes in one
 // pass.  A tie is a crossing of each axis of the pair at the same point, so
 // it is found from either side: for each pair the pass takes the crossings
@@ -788,13 +759,85 @@ __device__ __forceinline__ void put_entry(const FillOut& F, int o, int c, float 
   wk.add(v * __ldg(F.x + ((unsigned)c < (unsigned)F.nvox ? c : 0)));
 }
 
-// every crossing of axis A: one entry each.  Crossings the FP32 bounds
-// cannot settle are queued and redone exactly after the pass (no call in
-// the loop); *overflow when the queue was full.
-template <int DIM, int A, class SM>
-__device__ __forceinline__ void fill_axis(SM& sm, int nseg, int lane, const SimDev* Sg, const PathF64* p64,
-                                          const FillOut& F, Kahan& wk, bool& overflow) {
-  const int tot = axis_starts<A>(sm, nseg, lane);
+// The fill's two passes over a row: pass 0 takes the axis-0 crossings of the
+// row's segments in order; pass 1 the axis-1 crossings and, in 3D, after all
+// of them the axis-2 crossings (a few per row on paths that run across the
+// slices), so that these fill axis 1's last round instead of a round of
+// their own.  fill_plan sets up both passes' positions at once: one lane per
+// two segments (2 lane, 2 lane + 1), one warp scan for the axis-0 and axis-1
+// counts together (low and high 16 bits; every total is at most kCross <
+// 2^16, so no field carries into the other) and one for axis 2.
+struct FillPlan {
+  int tot0, tot1, tot;  // pass 0's positions; pass 1's axis-1 and all positions
+};
+
+// marks the runs of segments sa = 2 lane and sb = sa + 1 (na and nb items
+// from positions ba and bb) in bits and their segments in ord, from run k0
+// on; returns k0 + the number of runs marked
+__device__ __forceinline__ unsigned mark_pair(unsigned* bits, unsigned char* ord, unsigned k0, int na, int nb, int ba,
+                                              int bb, int sa, unsigned lt) {
+  const unsigned bal_a = __ballot_sync(0xffffffffu, na > 0), bal_b = __ballot_sync(0xffffffffu, nb > 0);
+  const unsigned r = k0 + __popc(bal_a & lt) + __popc(bal_b & lt);
+  if (na > 0) {
+    atomicOr(bits + (ba >> 5), 1u << (ba & 31));
+    ord[r] = (unsigned char)sa;
+  }
+  if (nb > 0) {
+    atomicOr(bits + (bb >> 5), 1u << (bb & 31));
+    ord[r + (na > 0 ? 1 : 0)] = (unsigned char)(sa + 1);
+  }
+  return k0 + __popc(bal_a) + __popc(bal_b);
+}
+
+template <int DIM, class SM>
+__device__ __forceinline__ FillPlan fill_plan(SM& sm, int nseg, int lane) {
+  const int sa = 2 * lane, sb = sa + 1;
+  int4 ca = make_int4(0, 0, 0, 0), cb = ca;
+  if (sa < nseg) ca = sm.cn[sa];
+  if (sb < nseg) cb = sm.cn[sb];
+  int t01, t2 = 0;
+  const int pa = ca.x | (ca.y << 16);
+  const int e01 = warp_excl_scan(pa + (cb.x | (cb.y << 16)), lane, &t01);
+  int e2 = 0;
+  if constexpr (DIM > 2) e2 = warp_excl_scan(ca.z + cb.z, lane, &t2);
+  FillPlan P;
+  P.tot0 = t01 & 0xffff;
+  P.tot1 = t01 >> 16;
+  P.tot = P.tot1 + t2;
+  const int b0a = e01 & 0xffff, b1a = e01 >> 16, b2a = P.tot1 + e2;
+  const int b0b = b0a + ca.x, b1b = b1a + ca.y, b2b = b2a + ca.z;
+  if (sa < nseg) {
+    sm.aux[sa] = b0a;
+    sm.aux1[sa] = b1a;
+    sm.aux2[sa] = b2a;
+  }
+  if (sb < nseg) {
+    sm.aux[sb] = b0b;
+    sm.aux1[sb] = b1b;
+    sm.aux2[sb] = b2b;
+  }
+  const int w0 = P.tot0 / 32 + 1, w1 = P.tot / 32 + 1;
+  for (int w = lane; w < w0; w += 32) sm.bits[w] = 0u;
+  for (int w = lane; w < w1; w += 32) sm.bits1[w] = 0u;
+  __syncwarp();
+  const unsigned lt = (1u << lane) - 1u;
+  mark_pair(sm.bits, sm.ord, 0u, ca.x, cb.x, b0a, b0b, sa, lt);
+  const unsigned k1 = mark_pair(sm.bits1, sm.ord1, 0u, ca.y, cb.y, b1a, b1b, sa, lt);
+  if constexpr (DIM > 2) mark_pair(sm.bits1, sm.ord1, k1, ca.z, cb.z, b2a, b2b, sa, lt);
+  __syncwarp();
+  return P;
+}
+
+// One pass: positions [0, tot1) are crossings of axis A1 (first position of
+// segment s: aux1[s]), [tot1, tot) crossings of axis A2 (aux2[s]; none when
+// A2 < 0).  One entry per crossing, written at its CSR position.  Crossings
+// the FP32 bounds cannot settle are queued and redone exactly after the pass
+// (no call in the loop); *overflow when the queue was full.
+template <int DIM, int A1, int A2, class SM>
+__device__ __forceinline__ void fill_pass(SM& sm, int tot1, int tot, const int* aux1, const int* aux2,
+                                          const unsigned* bits, const unsigned char* ord, int lane, const SimDev* Sg,
+                                          const PathF64* p64, const FillOut& F, Kahan& wk, bool& overflow) {
+  constexpr int B = A2 < 0 ? A1 : A2;
   if (lane == 0) sm.qn = 0;
   __syncwarp();
   int ordbase = 0;
@@ -802,7 +845,7 @@ __device__ __forceinline__ void fill_axis(SM& sm, int nseg, int lane, const SimD
   // the next round's work
   float pv = 0.f, px = 0.f;
   for (int p0 = 0; p0 < tot; p0 += 32) {
-    const int s = seg_at(sm.bits, sm.ord, p0, lane, ordbase);
+    const int s = seg_at(bits, ord, p0, lane, ordbase);
     const int p = p0 + lane;
     float v = 0.f, xv = 0.f;
     if (p < tot) {
@@ -811,102 +854,22 @@ __device__ __forceinline__ void fill_axis(SM& sm, int nseg, int lane, const SimD
       for (int c = 0; c < DIM; ++c) ax[c] = sm.ax[c][s];
       const int4 cn = sm.cn[s], dc = sm.dc[s];
       const float4 sf = sm.sf[s];
-      const int i = p - sm.aux[s];
-      bool unsure = false;
-      float ph;
-      const Cross cr = cross_x<DIM, A>(ax, cn, dc, sf.x, i, ph, unsure);
-      if (!unsure) {
-        v = fmaf(fmaxf(cr.nv - ph, 0.f), sf.y, cr.last ? sf.z : 0.f);
-        xv = put_entry_x(F, dc.w + cr.rank, cr.colv, v);
-      } else {
-        const int k = atomicAdd(&sm.qn, 1);
-        if (k < SM::kQ)
-          sm.q[k] = s | (i << 8);
-        else
-          overflow = true;
-      }
-    }
-    wk.add(pv * px);
-    pv = v;
-    px = xv;
-  }
-  wk.add(pv * px);
-  __syncwarp();
-  const int nq = min(sm.qn, SM::kQ);
-  for (int k = lane; k < nq; k += 32) {
-    const int s = sm.q[k] & 0xff, i = sm.q[k] >> 8;
-    const float4 sf = sm.sf[s];
-    const float ph = fmaf((float)i, sm.ax[A][s].y, sm.ax[A][s].x);
-    const Cross cr = cross_exact<DIM>(Sg, p64, s, fill_axes<DIM>(sm, s, A), i, sm.cn[s].w, sm.misc[s], sf.x);
-    const float v = fmaf(fmaxf(cr.nv - ph, 0.f), sf.y, cr.last ? sf.z : 0.f);
-    put_entry(F, sm.dc[s].w + cr.rank, cr.colv, v, wk);
-  }
-  __syncwarp();
-}
-
-// Crossings of axes 1 and 2 in one pass (3D): every axis-1 crossing of the
-// row's segments, then every axis-2 crossing (a few per row on paths that
-// run across the slices), so that the axis-2 crossings fill the last round
-// of axis 1 and only the round that straddles the two groups takes both
-// forms.  Otherwise as fill_axis.
-template <int DIM, class SM>
-__device__ __forceinline__ void fill_axes12(SM& sm, int nseg, int lane, const SimDev* Sg, const PathF64* p64,
-                                            const FillOut& F, Kahan& wk, bool& overflow) {
-  int n[2][2] = {{0, 0}, {0, 0}}, base[2][2], t[2][2];
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int s = lane + 32 * h;
-    if (s < nseg) {
-      n[0][h] = sm.cn[s].y;
-      n[1][h] = sm.cn[s].z;
-    }
-  }
-  base[0][0] = warp_excl_scan(n[0][0], lane, &t[0][0]);
-  base[0][1] = warp_excl_scan(n[0][1], lane, &t[0][1]) + t[0][0];
-  const int tot1 = t[0][0] + t[0][1];
-  base[1][0] = warp_excl_scan(n[1][0], lane, &t[1][0]) + tot1;
-  base[1][1] = warp_excl_scan(n[1][1], lane, &t[1][1]) + tot1 + t[1][0];
-  const int tot = tot1 + t[1][0] + t[1][1];
-  __syncwarp();  // the previous pass has finished reading aux, bits and ord
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int s = lane + 32 * h;
-    if (s < nseg) {
-      sm.aux[s] = base[0][h];
-      sm.aux2[s] = base[1][h];
-    }
-  }
-  mark_starts2(sm.bits, sm.ord, tot, n, base, lane);
-  if (lane == 0) sm.qn = 0;
-  __syncwarp();
-  int ordbase = 0;
-  float pv = 0.f, px = 0.f;
-  for (int p0 = 0; p0 < tot; p0 += 32) {
-    const int s = seg_at(sm.bits, sm.ord, p0, lane, ordbase);
-    const int p = p0 + lane;
-    float v = 0.f, xv = 0.f;
-    if (p < tot) {
-      float4 ax[DIM];
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) ax[c] = sm.ax[c][s];
-      const int4 cn = sm.cn[s], dc = sm.dc[s];
-      const float4 sf = sm.sf[s];
-      const bool second = p >= tot1;
-      const int i = p - (second ? sm.aux2[s] : sm.aux[s]);
+      const bool second = A2 >= 0 && p >= tot1;
+      const int i = p - (second ? aux2[s] : aux1[s]);
       bool unsure = false;
       float ph;
       Cross cr;
       if (!second)
-        cr = cross_x<DIM, 1>(ax, cn, dc, sf.x, i, ph, unsure);
+        cr = cross_x<DIM, A1>(ax, cn, dc, sf.x, i, ph, unsure);
       else
-        cr = cross_x<DIM, DIM - 1>(ax, cn, dc, sf.x, i, ph, unsure);
+        cr = cross_x<DIM, B>(ax, cn, dc, sf.x, i, ph, unsure);
       if (!unsure) {
         v = fmaf(fmaxf(cr.nv - ph, 0.f), sf.y, cr.last ? sf.z : 0.f);
         xv = put_entry_x(F, dc.w + cr.rank, cr.colv, v);
       } else {
         const int k = atomicAdd(&sm.qn, 1);
         if (k < SM::kQ)
-          sm.q[k] = s | ((second ? 2 : 1) << 8) | (i << 10);
+          sm.q[k] = s | ((second ? B : A1) << 8) | (i << 10);
         else
           overflow = true;
       }
@@ -1156,11 +1119,10 @@ __device__ __forceinline__ bool coop_fill_row(const SimDev& S, const MixArgs& M,
       F.hconst = (float)g.h[0];
       const PathF64* p64 = M.r64 + row;
       bool overflow = false;
-      fill_axis<DIM, 0>(sm, nseg, lane, Sg, p64, F, wk, overflow);
-      if constexpr (DIM > 2)
-        fill_axes12<DIM>(sm, nseg, lane, Sg, p64, F, wk, overflow);
-      else
-        fill_axis<DIM, 1>(sm, nseg, lane, Sg, p64, F, wk, overflow);
+      const FillPlan P = fill_plan<DIM>(sm, nseg, lane);
+      fill_pass<DIM, 0, -1>(sm, P.tot0, P.tot0, sm.aux, sm.aux, sm.bits, sm.ord, lane, Sg, p64, F, wk, overflow);
+      fill_pass<DIM, 1, (DIM > 2 ? 2 : -1)>(sm, P.tot1, P.tot, sm.aux1, sm.aux2, sm.bits1, sm.ord1, lane, Sg, p64, F,
+                                              wk, overflow);
       // 2. entry 0 of every segment that does not continue the previous one
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -1184,6 +1146,16 @@ __device__ __forceinline__ bool coop_fill_row(const SimDev& S, const MixArgs& M,
           sum = df_add(sum, o);
         }
         if (lane == 0) b[row] = (sum.hi + sum.lo) * r.fac;
+        // entries written against row_ptr's range: the last segment's first
+        // slot in the row plus its entries (each crossing, and its first
+        // entry unless it continues the previous segment)
+        if (lane == 0) {
+          const int misc = sm.misc[nseg - 1];
+          const int4 cn = sm.cn[nseg - 1];
+          const int first = (misc & kMergeBit) ? 0 : 1;
+          const int e = (misc & 3) == kStRegular ? cn.x + cn.y + cn.z + first : 0;
+          if (sm.dc[nseg - 1].w - first + e != F.len) note_row_mismatch(S);
+        }
         __syncwarp();
         return true;
       }

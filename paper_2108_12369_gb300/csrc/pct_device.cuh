@@ -66,7 +66,15 @@ struct SimDev {
   double R;               // lead-in / lead-out length: 2 x grid diagonal
   const double2* cs;      // [n_angles] (cos, sin) from the host's libm
   const Basis4* basis;    // [K + 1] Hermite basis at s = j / K
+  // rows whose fill wrote a different number of entries than row_ptr gives
+  // them (the workspace's first word; zeroed by the count)
+  unsigned long long* status;
 };
+
+// a row of the fill whose entry count differs from its row_ptr range
+__device__ __forceinline__ void note_row_mismatch(const SimDev& S) {
+  if (S.status) atomicAdd(S.status, 1ULL);
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon et al., SC'11).  key = (seed, stream),

@@ -23,13 +23,15 @@ struct FillSinkF64 {
   int* col;
   float* val;
   const float* x;
-  long long pos;
+  long long pos, end;  // next position, the end of the row's range (stores stay inside)
   double b;
   bool constant;
   float hconst;
   __device__ void put(int c, double len) {
-    col[pos] = c;
-    val[pos] = constant ? hconst : (float)len;
+    if (pos < end) {
+      col[pos] = c;
+      val[pos] = constant ? hconst : (float)len;
+    }
     ++pos;
     b = b + len * (double)__ldg(x + c);
   }
@@ -75,10 +77,12 @@ __global__ void k_fill_f64(SimDev S, long long row0, long long n, const long lon
   fs.val = val;
   fs.x = x;
   fs.pos = row_ptr[i];
+  fs.end = row_ptr[i + 1];
   fs.b = 0.0;
   fs.constant = (S.md.chord == PCT_CHORD_CONSTANT);
   fs.hconst = (float)S.ph.g.h[0];
   walk_path_f64(S, p, fs);
+  if (fs.pos != fs.end) note_row_mismatch(S);
   double bb = fs.b;
   if (S.md.noise == PCT_NOISE_GAUSS_REL) bb = bb * (1.0 + S.md.noise_rel * p.z_noise);
   b[i] = (float)bb;

@@ -72,7 +72,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 # every symbol include/pct.h declares
 EXPORTS = ["pct_phantom_create", "pct_phantom_destroy", "pct_phantom_nvox", "pct_phantom_rasterize",
            "pct_simulate_workspace_size", "pct_simulate_count", "pct_simulate_fill", "pct_simulate_fill_host",
-           "pct_simulate_host_workspace_size", "pct_simulate_host", "pct_simulate",
+           "pct_simulate_host_workspace_size", "pct_simulate_host", "pct_simulate_check", "pct_simulate",
            "pct_projector_workspace_size", "pct_forward", "pct_adjoint", "pct_batch_workspace_size", "pct_batch_create",
            "pct_batch_count", "pct_batch_nnz", "pct_batch_fill", "pct_batch_params", "pct_batch_destroy",
            "pct_scan_counts_static", "pct_sap_workspace_size", "pct_sap", "pct_csr_file_create",
@@ -105,6 +105,7 @@ def lib():
             "pct_simulate_host_workspace_size": ([vp, P(Geometry), C.c_int32, C.c_int32, P(C.c_size_t)], C.c_int),
             "pct_simulate_host": ([vp, P(Geometry), C.c_int32, C.c_int32, vp, C.c_size_t, vp, vp, C.c_size_t, vp, vp,
                                    vp, vp, C.c_int64, P(C.c_int64), vp], C.c_int),
+            "pct_simulate_check": ([vp, P(C.c_int64), vp], C.c_int),
             "pct_simulate": ([vp, P(Geometry), C.c_int32, ALLOC_FN, FREE_FN, vp, P(Csr), vp], C.c_int),
             "pct_projector_workspace_size": ([vp, P(Geometry), C.c_int32, C.c_int64, P(C.c_size_t)],
                                              C.c_int),
@@ -241,6 +242,14 @@ def simulate_fill_host(ph, geo, precision, workspace, row_ptr, x_true, staging, 
                                         workspace.numel() * workspace.element_size(), _ptr(row_ptr),
                                         _ptr(x_true), _ptr(staging), staging.numel() * staging.element_size(),
                                         _ptr(row_ptr_h), _ptr(col_h), _ptr(val_h), _ptr(b_h), _stream(stream)))
+
+
+def simulate_check(workspace, stream=None) -> int:
+    """Rows whose fill disagreed with row_ptr since the count that used this
+    workspace (synchronises the stream); 0 for a consistent fill."""
+    n = C.c_int64()
+    _check(lib().pct_simulate_check(_ptr(workspace), C.byref(n), _stream(stream)))
+    return n.value
 
 
 def simulate_host_workspace_size(ph: Phantom, geo: GeometryArgs, precision: int, angles_per_block: int) -> int:

@@ -144,6 +144,8 @@ def test_simulate_host_validates_before_any_device_work(pct):
     assert call(2, 1 << 40, None, stg, p, p, 10, C.byref(nnz), "NULL argument") == pct.EINVAL
     assert call(2, 1 << 40, p, stg, p, None, 10, C.byref(nnz), "NULL col_host") == pct.EINVAL
     assert call(2, 1 << 40, p, odd, p, p, 10, C.byref(nnz), "aligned") == pct.EINVAL
+    assert L.pct_simulate_check(None, C.byref(nnz), None) == pct.EINVAL
+    assert L.pct_simulate_check(p, None, None) == pct.EINVAL
     need = pct.simulate_host_workspace_size(ph, geo, pct.PREC_MIXED, 2)
     buf[0] = 7
     assert call(2, need - 1, p, stg, p, None, 0, C.byref(nnz), "workspace") == pct.ENOMEM
