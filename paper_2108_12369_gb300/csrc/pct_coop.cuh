@@ -351,28 +351,6 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane, int* total) {
   return x - v;
 }
 
-// Mark in `bits` the start (base[h]) of every segment with a nonzero count
-// and record its ordinal -> segment map; lanes hold segments lane, lane + 32.
-__device__ __forceinline__ void mark_starts(unsigned* bits, unsigned char* ord, int total, const int (&cnt)[2],
-                                            const int (&base)[2], int lane) {
-  const int nwords = (total + 31) / 32 + 1;
-  for (int w = lane; w < nwords; w += 32) bits[w] = 0u;
-  __syncwarp();
-  const unsigned lt = (1u << lane) - 1u;
-  unsigned prev = 0;
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const bool on = cnt[h] > 0;
-    const unsigned bal = __ballot_sync(0xffffffffu, on);
-    if (on) {
-      atomicOr(bits + (base[h] >> 5), 1u << (base[h] & 31));
-      ord[prev + __popc(bal & lt)] = (unsigned char)(lane + 32 * h);
-    }
-    prev += __popc(bal);
-  }
-  __syncwarp();
-}
-
 // segment of crossing position p in round p0 (positions p0 .. p0 + 31 lie in
 // bitmap word p0 / 32); ordbase counts the starts of earlier rounds
 __device__ __forceinline__ int seg_at(const unsigned* bits, const unsigned char* ord, int p0, int lane, int& ordbase) {
@@ -597,21 +575,22 @@ static __device__ __noinline__ bool tie_exact(const SimDev* Sg, const PathF64* p
          0;
 }
 
-// Items of a pass over the row's segments, 32 per round (segment s on lane
-// s % 32 holds n[s / 32] of them): marks each segment's first one and
-// returns their number (positions are counted segment after segment;
-// sm.aux[s] = segment s's first position).
-template <class SM>
-__device__ __forceinline__ int pass_starts(SM& sm, int nseg, int lane, const int (&n)[2]) {
-  int base[2], t0, t1;
-  base[0] = warp_excl_scan(n[0], lane, &t0);
-  base[1] = warp_excl_scan(n[1], lane, &t1) + t0;
-  __syncwarp();  // the previous pass has finished reading aux, bits and ord
-#pragma unroll
-  for (int h = 0; h < 2; ++h)
-    if (lane + 32 * h < nseg) sm.aux[lane + 32 * h] = base[h];
-  mark_starts(sm.bits, sm.ord, t0 + t1, n, base, lane);
-  return t0 + t1;
+// marks the runs of segments sa = 2 lane and sb = sa + 1 (na and nb items
+// from positions ba and bb) in bits and their segments in ord, from run k0
+// on; returns k0 + the number of runs marked
+__device__ __forceinline__ unsigned mark_pair(unsigned* bits, unsigned char* ord, unsigned k0, int na, int nb, int ba,
+                                              int bb, int sa, unsigned lt) {
+  const unsigned bal_a = __ballot_sync(0xffffffffu, na > 0), bal_b = __ballot_sync(0xffffffffu, nb > 0);
+  const unsigned r = k0 + __popc(bal_a & lt) + __popc(bal_b & lt);
+  if (na > 0) {
+    atomicOr(bits + (ba >> 5), 1u << (ba & 31));
+    ord[r] = (unsigned char)sa;
+  }
+  if (nb > 0) {
+    atomicOr(bits + (bb >> 5), 1u << (bb & 31));
+    ord[r + (na > 0 ? 1 : 0)] = (unsigned char)(sa + 1);
+  }
+  return k0 + __popc(bal_a) + __popc(bal_b);
 }
 
 // Exact ties between crossings of different axes, every pair of axes in one
@@ -625,10 +604,12 @@ template <int DIM, class SM>
 __device__ __forceinline__ void tie_pass(SM& sm, int nseg, int lane, const SimDev* Sg, const PathF64* p64, bool& tie,
                                          bool& overflow) {
   using W = SegW<DIM>;
+  // positions: one lane per two segments (2 lane, 2 lane + 1), one scan
+  const int sa = 2 * lane;
   int n[2] = {0, 0};
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    const int s = lane + 32 * h;
+    const int s = sa + h;
     if (s < nseg) {
       const int n0 = sm.cnt(s, 0), n1 = sm.cnt(s, 1);
       n[h] = min(n0, n1);
@@ -638,8 +619,14 @@ __device__ __forceinline__ void tie_pass(SM& sm, int nseg, int lane, const SimDe
       }
     }
   }
-  const int tot = pass_starts(sm, nseg, lane, n);
+  int tot;
+  const int ba = warp_excl_scan(n[0] + n[1], lane, &tot), bb = ba + n[0];
+  if (sa < nseg) sm.aux[sa] = ba;
+  if (sa + 1 < nseg) sm.aux[sa + 1] = bb;
+  for (int w = lane; w < tot / 32 + 1; w += 32) sm.bits[w] = 0u;
   if (lane == 0) sm.qn = 0;
+  __syncwarp();
+  mark_pair(sm.bits, sm.ord, 0u, n[0], n[1], ba, bb, sa, (1u << lane) - 1u);
   __syncwarp();
   int ordbase = 0;
   for (int p0 = 0; p0 < tot; p0 += 32) {
@@ -770,24 +757,6 @@ __device__ __forceinline__ void put_entry(const FillOut& F, int o, int c, float 
 struct FillPlan {
   int tot0, tot1, tot;  // pass 0's positions; pass 1's axis-1 and all positions
 };
-
-// marks the runs of segments sa = 2 lane and sb = sa + 1 (na and nb items
-// from positions ba and bb) in bits and their segments in ord, from run k0
-// on; returns k0 + the number of runs marked
-__device__ __forceinline__ unsigned mark_pair(unsigned* bits, unsigned char* ord, unsigned k0, int na, int nb, int ba,
-                                              int bb, int sa, unsigned lt) {
-  const unsigned bal_a = __ballot_sync(0xffffffffu, na > 0), bal_b = __ballot_sync(0xffffffffu, nb > 0);
-  const unsigned r = k0 + __popc(bal_a & lt) + __popc(bal_b & lt);
-  if (na > 0) {
-    atomicOr(bits + (ba >> 5), 1u << (ba & 31));
-    ord[r] = (unsigned char)sa;
-  }
-  if (nb > 0) {
-    atomicOr(bits + (bb >> 5), 1u << (bb & 31));
-    ord[r + (na > 0 ? 1 : 0)] = (unsigned char)(sa + 1);
-  }
-  return k0 + __popc(bal_a) + __popc(bal_b);
-}
 
 template <int DIM, class SM>
 __device__ __forceinline__ FillPlan fill_plan(SM& sm, int nseg, int lane) {
