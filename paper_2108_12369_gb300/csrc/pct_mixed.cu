@@ -182,15 +182,17 @@ __device__ __forceinline__ void fill_block(const SimDev& S, const MixArgs& M, co
   for (int q = threadIdx.x >> 5; q < n_walk; q += 4) fill_row_walk<DIM>(Sg, M, row0 + walk[q], row_ptr, x, col, val, b);
 }
 
-// 3D rows are shorter (fewer crossings per segment): 8 blocks per SM pay
-// off there (3D head fill -5 %), 7 in 2D (NEO-2 fill +2 % at 8)
-template <int DIM>
+// 3D rows are shorter (fewer crossings per segment): more resident blocks
+// pay off there (3D head fill: 8 blocks per SM -5 % against 7, 9 blocks a
+// further -1 %, 10 blocks +22 %), 7 in 2D (NEO-2 fill +2 % at 8, no change
+// at 9).  The lean form's larger shared layout holds it to 8.
+template <int DIM, bool LEAN = false>
 constexpr int fill_blocks_per_sm() {
-  return DIM == 3 ? 8 : 7;
+  return DIM == 3 ? (LEAN ? 8 : 9) : 7;
 }
 
 template <int DIM, int CAP, bool LEAN>
-__global__ void __launch_bounds__(128, fill_blocks_per_sm<DIM>()) k_fill_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
+__global__ void __launch_bounds__(128, fill_blocks_per_sm<DIM, LEAN>()) k_fill_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
                                                     long long n, const long long* __restrict__ row_ptr,
                                                     const float* __restrict__ x, int* __restrict__ col,
                                                     float* __restrict__ val, float* __restrict__ b) {
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(128, fill_blocks_per_sm<DIM>()) k_fill_mixed(S
 // rows [row_begin, n) only (a kernel of its own, so that the whole fill
 // keeps its first row at compile-time zero)
 template <int DIM, int CAP, bool LEAN>
-__global__ void __launch_bounds__(128, fill_blocks_per_sm<DIM>()) k_fill_mixed_range(SimDev S, MixArgs M, const SimDev* Sg,
+__global__ void __launch_bounds__(128, fill_blocks_per_sm<DIM, LEAN>()) k_fill_mixed_range(SimDev S, MixArgs M, const SimDev* Sg,
                                                           const GridDF* gdg, long long n,
                                                           const long long* __restrict__ row_ptr,
                                                           const float* __restrict__ x, int* __restrict__ col,
@@ -229,7 +231,7 @@ __device__ __forceinline__ int batch_find(const BatchInst* __restrict__ B, int n
 // phases: 0 path set-up, 1 count, 2 fill (the launch bounds follow the
 // per-simulation kernels of each phase)
 template <int kPhase, int DIM, int CAP, bool LEAN>
-__global__ void __launch_bounds__(128, kPhase == 0 ? 1 : (kPhase == 1 ? 8 : fill_blocks_per_sm<DIM>()))
+__global__ void __launch_bounds__(128, kPhase == 0 ? 1 : (kPhase == 1 ? 8 : fill_blocks_per_sm<DIM, LEAN>()))
     k_batch(const BatchInst* __restrict__ B, int n_inst, long long first, long long last,
             unsigned long long* next, int nr, int pf) {
   __shared__ long long item_s;
