@@ -121,9 +121,15 @@ __device__ __forceinline__ void rows_block(const SimDev& S, const MixArgs& M, co
   for (int q = threadIdx.x >> 5; q < n_walk; q += 4) count_row_walk<DIM>(Sg, M, row0 + walk[q], counts);
 }
 
-// The count of one simulation runs as two kernels: the FP64 path set-up
-// (lane per row) and the warp-cooperative count (warp per row), so that
-// each kernel's code stays small enough for the instruction caches.
+// count blocks resident per SM (64 -> 56 registers a thread: 3D head count
+// -3 %, NEO-2 -3 % against 8 blocks)
+constexpr int kCountBlocksPerSm = 9;
+
+// The count of one simulation runs as three kernels: the FP64 path set-up
+// (lane per row), the lead segments' set-up (lane per row) and the
+// warp-cooperative count (warp per row), so that each kernel's code stays
+// small enough for the instruction caches and the FP64 kernel keeps its
+// occupancy.
 template <int DIM>
 __global__ void __launch_bounds__(128) k_path_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
                                                     long long n) {
@@ -137,7 +143,7 @@ __global__ void __launch_bounds__(128) k_lead_mixed(SimDev S, MixArgs M, const S
 }
 
 template <int DIM, int CAP>
-__global__ void __launch_bounds__(128, 8) k_count_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
+__global__ void __launch_bounds__(128, kCountBlocksPerSm) k_count_mixed(SimDev S, MixArgs M, const SimDev* Sg, const GridDF* gdg,
                                                      long long n, long long* __restrict__ counts) {
   rows_block<DIM, CAP>(S, M, Sg, gdg, n, (long long)blockIdx.x * blockDim.x, counts);
 }
@@ -231,7 +237,7 @@ __device__ __forceinline__ int batch_find(const BatchInst* __restrict__ B, int n
 // phases: 0 path set-up, 1 count, 2 fill (the launch bounds follow the
 // per-simulation kernels of each phase)
 template <int kPhase, int DIM, int CAP, bool LEAN>
-__global__ void __launch_bounds__(128, kPhase == 0 ? 1 : (kPhase == 1 ? 8 : fill_blocks_per_sm<DIM, LEAN>()))
+__global__ void __launch_bounds__(128, kPhase == 0 ? 1 : (kPhase == 1 ? kCountBlocksPerSm : fill_blocks_per_sm<DIM, LEAN>()))
     k_batch(const BatchInst* __restrict__ B, int n_inst, long long first, long long last,
             unsigned long long* next, int nr, int pf) {
   __shared__ long long item_s;
