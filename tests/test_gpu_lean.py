@@ -2,8 +2,8 @@
 records, the fill sets each row's segments up again with the count's own
 code.  Its output must equal the mixed form's bit for bit -- row pointers,
 indices, values and WEPL -- on regular rows, on rows the cooperative form
-hands to the per-lane walker (exact ties on axis-aligned and lattice-diagonal
-rays, rows beyond the cooperative limits), through the host-memory fill, and
+hands to the per-lane walker (near-degenerate segments of axis-aligned and
+lattice-diagonal rays, rows beyond the cooperative limits), through the host-memory fill, and
 inside a lean batch; and it needs a fraction of the workspace."""
 import math
 

@@ -142,8 +142,10 @@ def test_extruded_and_constant_chord(pct, orc, prec):
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_axis_aligned_angles_and_grid_edges(pct, orc, prec):
-    """Angles 0, 90, 180, 270 degrees put straight paths along grid planes
-    and exact ties at every corner; offsets span beyond the grid."""
+    """Angles 0, 90, 180, 270 degrees put straight paths along grid lines (an
+    axis with no or nearly no extent: inert, or a segment the walker takes);
+    45 and 135 degrees send them near lattice corners (near-ties the FP64
+    definition decides); offsets span beyond the grid."""
     w = W.neo1_2d_straight(n_angles=4, paths_per_angle=2000)
     w["angles"] = np.array([0.0, math.pi / 2, math.pi, 1.5 * math.pi])
     w["model"] = W.model(W.STRAIGHT, (-130.0, 130.0))
