@@ -320,9 +320,15 @@ typedef struct {
 typedef struct pct_batch pct_batch; /* opaque */
 
 #define PCT_BATCH_AUTOTUNE 1 /* flags: time the launch shapes once and keep the fastest */
-#define PCT_BATCH_LEAN 2     /* flags: every item in the PCT_PREC_MIXED_LEAN form (small workspace) */
+/* flags: items may take the PCT_PREC_MIXED_LEAN form (small workspace).  The
+ * workspace size is then that of every item in the lean form; any workspace
+ * given beyond it holds segment records, and the largest items take the
+ * full PCT_PREC_MIXED form (whose fill is faster) while their records fit.
+ * The outputs are the same bits either way. */
+#define PCT_BATCH_LEAN 2
 
-/* bytes of device workspace pct_batch_create needs for these items and flags */
+/* bytes of device workspace pct_batch_create needs for these items and flags
+ * (with PCT_BATCH_LEAN: the all-lean minimum) */
 pct_status pct_batch_workspace_size(const pct_batch_item* items, int32_t n, int32_t flags, size_t* bytes);
 
 /* Uploads every simulation's tables into the workspace, orders the work

@@ -758,7 +758,10 @@ struct pct_batch {
   unsigned long long* d_next = nullptr;   // two counters (2D, 3D launches)
   long long first3[3] = {0, 0, 0}, total[3] = {0, 0, 0};  // per phase: first 3D work item, work items
   pct_batch_tuning tune;                  // the launch shape in use
-  bool lean = false;        // PCT_BATCH_LEAN: no segment records, fills rebuild the tables
+  bool lean = false;        // PCT_BATCH_LEAN: instances may take the lean form
+  std::vector<char> lean_k; // by item: the lean form (no segment records, the fill rebuilds the table)
+  long long f2[2][2][2] = {};  // fill phase: [dim 3][lean] first and last work item
+  int bps2[2][2] = {{1, 1}, {1, 1}};  // fill phase: resident blocks per SM [dim 3][lean]
   bool autotune = false;
   bool fill_tuned = false;  // the fill's shape was timed (or taken from the cache)
   unsigned long long sig = 0;
@@ -798,6 +801,7 @@ unsigned long long batch_signature(const pct_batch& b) {
   mix(b.lean ? 1ULL : 0ULL);
   for (int k = 0; k < b.n; ++k) {
     const pct_batch_item& it = b.items[k];
+    mix(b.lean_k[k] ? 1ULL : 0ULL);
     mix((unsigned long long)it.phantom->dev.g.dim);
     for (int a = 0; a < 3; ++a) mix((unsigned long long)it.phantom->dev.g.n[a]);
     mix((unsigned long long)b.layouts[k].rows);
@@ -806,9 +810,10 @@ unsigned long long batch_signature(const pct_batch& b) {
   return h;
 }
 
-// Processing order (2D instances first, then 3D; within each, item order or
-// largest first) and each phase's work items of rows_per_item[phase] rows;
-// uploads the instance table (with the outputs set so far).
+// Processing order (2D instances first, then 3D; within each, the full form
+// before the lean form, then item order or largest first) and each phase's
+// work items of rows_per_item[phase] rows; uploads the instance table (with
+// the outputs set so far).
 pct_status batch_arrange(pct_batch& b, cudaStream_t st) {
   const int n = b.n;
   std::vector<int> ord(n);
@@ -816,6 +821,7 @@ pct_status batch_arrange(pct_batch& b, cudaStream_t st) {
   std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
     const int dx = b.items[x].phantom->dev.g.dim, dy = b.items[y].phantom->dev.g.dim;
     if (dx != dy) return dx < dy;
+    if (b.lean_k[x] != b.lean_k[y]) return b.lean_k[x] < b.lean_k[y];
     if (b.tune.order == 1) return b.layouts[x].rows > b.layouts[y].rows;
     return false;
   });
@@ -840,6 +846,22 @@ pct_status batch_arrange(pct_batch& b, cudaStream_t st) {
     b.total[p] = item;
     if (b.first3[p] < 0) b.first3[p] = item;
   }
+  // the fill phase's four launches: [dim 3][lean], each a contiguous item range
+  {
+    const long long R = b.tune.rows_per_item[2];
+    for (int d = 0; d < 2; ++d)
+      for (int l = 0; l < 2; ++l) b.f2[d][l][0] = b.f2[d][l][1] = 0;
+    bool seen[2][2] = {{false, false}, {false, false}};
+    for (int pos = 0; pos < n; ++pos) {
+      const int d = b.inst[pos].S.ph.g.dim == 3 ? 1 : 0, l = b.lean_k[ord[pos]] ? 1 : 0;
+      const long long i0 = b.inst[pos].item0[2], i1 = i0 + (b.inst[pos].n + R - 1) / R;
+      if (!seen[d][l]) {
+        b.f2[d][l][0] = i0;
+        seen[d][l] = true;
+      }
+      b.f2[d][l][1] = i1;
+    }
+  }
   if (cudaMemcpyAsync(b.d_inst, b.inst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return cuda_check("batch table upload");
@@ -848,6 +870,15 @@ pct_status batch_arrange(pct_batch& b, cudaStream_t st) {
 
 void batch_launch_phase(pct_batch& b, int f, cudaStream_t st) {
   const pct_batch_tuning& t = b.tune;
+  if (f == 2) {
+    // full-form instances, then lean ones, per dimensionality (the
+    // launches run in stream order, so two counters serve all four)
+    for (int d = 0; d < 2; ++d)
+      for (int l = 0; l < 2; ++l)
+        launch_batch(2, d == 0 ? 2 : 3, b.small[d], l != 0, b.d_inst, b.n, b.f2[d][l][0], b.f2[d][l][1],
+                     b.d_next + l, b.sms * b.bps2[d][l] * t.grid_mult[2], t.rows_per_item[2], t.fill_prefetch, st);
+    return;
+  }
   launch_batch(f, 2, b.small[0], b.lean, b.d_inst, b.n, 0, b.first3[f], b.d_next,
                b.sms * b.bps[f][0] * t.grid_mult[f], t.rows_per_item[f], t.fill_prefetch, st);
   launch_batch(f, 3, b.small[1], b.lean, b.d_inst, b.n, b.first3[f], b.total[f], b.d_next + 1,
@@ -983,6 +1014,27 @@ extern "C" pct_status pct_batch_create(const pct_batch_item* items, int32_t n, v
   if (!b) return fail(PCT_ENOMEM, "out of host memory");
   b->n = n;
   b->lean = form == PCT_PREC_MIXED_LEAN;
+  b->lean_k.assign(n, b->lean ? 1 : 0);
+  if (b->lean) {
+    // the workspace beyond the all-lean size holds segment records: the
+    // largest instances take the full form (a fill twice as fast) while
+    // their records fit
+    size_t spare = ws_bytes - need;
+    std::vector<int> by_rows(n);
+    for (int k = 0; k < n; ++k) by_rows[k] = k;
+    std::stable_sort(by_rows.begin(), by_rows.end(), [&](int x, int y) {
+      return (long long)items[x].geo.n_angles * items[x].geo.paths_per_angle >
+             (long long)items[y].geo.n_angles * items[y].geo.paths_per_angle;
+    });
+    for (int k : by_rows) {
+      const size_t full = align256(layout_of(items[k].phantom, &items[k].geo, PCT_PREC_MIXED).total);
+      const size_t lean = align256(layout_of(items[k].phantom, &items[k].geo, PCT_PREC_MIXED_LEAN).total);
+      if (full > lean && full - lean <= spare) {
+        b->lean_k[k] = 0;
+        spare -= full - lean;
+      }
+    }
+  }
   b->autotune = (flags & PCT_BATCH_AUTOTUNE) != 0;
   b->tune = default_tuning();
   b->items.assign(items, items + n);
@@ -996,14 +1048,15 @@ extern "C" pct_status pct_batch_create(const pct_batch_item* items, int32_t n, v
   size_t off = 0;
   for (int k = 0; k < n; ++k) {
     const pct_batch_item& it = items[k];
-    Layout L = layout_of(it.phantom, &it.geo, form);
+    const int form_k = b->lean_k[k] ? PCT_PREC_MIXED_LEAN : PCT_PREC_MIXED;
+    Layout L = layout_of(it.phantom, &it.geo, form_k);
     if (L.rows > 0 && (!it.row_ptr_dev || !it.x_true_dev)) {
       pct_batch_destroy(b);
       return fail(PCT_EINVAL, "batch item %d: NULL row_ptr_dev or x_true_dev", k);
     }
     b->base[k] = off;
     Layout L2;
-    rc = make_sim(it.phantom, &it.geo, form, base + off, L.total, st, b->sims[k], L2);
+    rc = make_sim(it.phantom, &it.geo, form_k, base + off, L.total, st, b->sims[k], L2);
     if (rc != PCT_OK) {
       pct_batch_destroy(b);
       return rc;
@@ -1024,7 +1077,7 @@ extern "C" pct_status pct_batch_create(const pct_batch_item* items, int32_t n, v
     memset(&I, 0, sizeof(I));
     I.S = b->sims[k];
     I.M = mix_args(b->sims[k], b->layouts[k].rows, (const char*)b->sims[k].cs - b->layouts[k].cs + b->layouts[k].basis32,
-                   (char*)b->sims[k].cs - b->layouts[k].cs + b->layouts[k].rec, b->lean);
+                   (char*)b->sims[k].cs - b->layouts[k].cs + b->layouts[k].rec, b->lean_k[k] != 0);
     I.n = b->layouts[k].rows;
     I.row_ptr_w = (long long*)items[k].row_ptr_dev;
     I.row_ptr = (const long long*)items[k].row_ptr_dev;
@@ -1033,6 +1086,8 @@ extern "C" pct_status pct_batch_create(const pct_batch_item* items, int32_t n, v
   }
   for (int f = 0; f < 3; ++f)
     for (int d = 0; d < 2; ++d) b->bps[f][d] = batch_blocks_per_sm(f, d == 0 ? 2 : 3, b->small[d], b->lean);
+  for (int d = 0; d < 2; ++d)
+    for (int l = 0; l < 2; ++l) b->bps2[d][l] = batch_blocks_per_sm(2, d == 0 ? 2 : 3, b->small[d], l != 0);
   b->sig = batch_signature(*b);
   bool cached = false;
   {

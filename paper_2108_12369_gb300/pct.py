@@ -363,7 +363,10 @@ class Batch:
     """pct_batch_* over a list of workload dicts: one persistent launch per
     phase for all of them, replayed from CUDA graphs."""
 
-    def __init__(self, workloads, autotune: bool = False, stream=None, device="cuda", lean: bool = False):
+    def __init__(self, workloads, autotune: bool = False, stream=None, device="cuda", lean: bool = False,
+                 workspace_bytes: int = 0):
+        """lean: items may take the lean form; workspace_bytes beyond the
+        all-lean size lets the largest items keep the full form."""
         import torch
         self.n = len(workloads)
         self.phantoms = [Phantom(w["phantom"]) for w in workloads]
@@ -376,9 +379,10 @@ class Batch:
         nbytes = C.c_size_t()
         flags = (BATCH_AUTOTUNE if autotune else 0) | (BATCH_LEAN if lean else 0)
         _check(lib().pct_batch_workspace_size(self._items, self.n, flags, C.byref(nbytes)))
-        self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=device)
+        size = max(nbytes.value, int(workspace_bytes))
+        self.workspace = torch.empty(size, dtype=torch.uint8, device=device)
         self.handle = C.c_void_p()
-        _check(lib().pct_batch_create(self._items, self.n, _ptr(self.workspace), nbytes.value,
+        _check(lib().pct_batch_create(self._items, self.n, _ptr(self.workspace), size,
                                       flags, _stream(stream),
                                       C.byref(self.handle)))
         self.device = device
@@ -392,12 +396,16 @@ class Batch:
         return [int(v) for v in out]
 
     def fill(self, nnz=None, stream=None):
-        """Allocates col / val / b per simulation and runs the fill phase."""
+        """Allocates col / val / b per simulation (kept for the next fill of
+        the same sizes) and runs the fill phase."""
         import torch
         nnz = self.nnz(stream) if nnz is None else nnz
-        self.col = [torch.empty(max(z, 1), dtype=torch.int32, device=self.device) for z in nnz]
-        self.val = [torch.empty(max(z, 1), dtype=torch.float32, device=self.device) for z in nnz]
-        self.b = [torch.empty(max(g.n_rows, 1), dtype=torch.float32, device=self.device) for g in self.geos]
+        if getattr(self, "_sizes", None) != list(nnz):  # outputs of the previous fill are reused
+            self.col = self.val = None  # freed before the new ones are allocated
+            self.col = [torch.empty(max(z, 1), dtype=torch.int32, device=self.device) for z in nnz]
+            self.val = [torch.empty(max(z, 1), dtype=torch.float32, device=self.device) for z in nnz]
+            self.b = [torch.empty(max(g.n_rows, 1), dtype=torch.float32, device=self.device) for g in self.geos]
+            self._sizes = list(nnz)
         cols = (C.c_void_p * self.n)(*[t.data_ptr() for t in self.col])
         vals = (C.c_void_p * self.n)(*[t.data_ptr() for t in self.val])
         bs = (C.c_void_p * self.n)(*[t.data_ptr() for t in self.b])

@@ -56,3 +56,24 @@ def test_batch_member_matches_oracle(pct, orc):
     torch.cuda.synchronize()
     ref = orc.simulate(w["phantom"], w["angles"], w["paths_per_angle"], w["model"], w["seed"], threads=8)
     compare(out, ref)
+
+
+@pytest.mark.parametrize("share", [0.0, 0.5, 1.0])
+def test_batch_with_both_forms(pct, share):
+    """PCT_BATCH_LEAN with workspace beyond the all-lean size: the largest
+    instances keep the full form (their fills run as full-form launches, the
+    rest as lean ones); every output equals its standalone run bit for bit."""
+    ws = _instances()
+    lean_min = pct.batch_workspace_size(ws, lean=True)
+    full = pct.batch_workspace_size(ws)
+    assert full > lean_min
+    batch = pct.Batch(ws, autotune=True, lean=True, workspace_bytes=lean_min + int(share * (full - lean_min)))
+    for rep in range(2):
+        batch.count()
+        outs = batch.fill()
+        torch.cuda.synchronize()
+        for w, o in zip(ws, outs):
+            ref = pct.simulate(pct.Phantom(w["phantom"]), pct.GeometryArgs(w), pct.PREC_MIXED)
+            torch.cuda.synchronize()
+            for k in ("row_ptr", "col", "val", "b", "x_true"):
+                assert torch.equal(o[k], ref[k]), (w["name"], k, share)
